@@ -1,0 +1,170 @@
+/*
+ * cc.h -- C ABI of the GB300 library for parallel correlation clustering.
+ *
+ * Implements the bulk-synchronous round of C4 and ClusterWild! and the
+ * disagreement objective from "Parallel Correlation Clustering on Big Graphs"
+ * (Pan, Papailiopoulos, Oymak, Recht, Ramchandran, Jordan; NIPS 2015).
+ *
+ * Problem (Sec. 2, definition of correlation clustering): a complete signed
+ * graph on n vertices is given by its positive edges as a symmetric CSR; every
+ * other pair is a negative edge.  A clustering is scored by its disagreements:
+ * positive edges between clusters plus negative pairs inside clusters.
+ *
+ * Method (Alg. 2): pi is a random order of the vertices.  Each round
+ *   1. Delta = maximum residual degree of the unclustered graph,
+ *   2. A = the next ceil(eps * n_i / Delta) unclustered vertices of pi,
+ *   3. centers: all of A (ClusterWild!), or the vertices of A with no
+ *      earlier-ranked center among their neighbours (C4; the greedy maximal
+ *      independent set of A in pi order),
+ *   4. every unclustered neighbour joins its lowest-ranked adjacent center
+ *      (createCluster; concurrency rule 2 of Sec. 2.1),
+ *   5. clustered vertices leave the graph and residual degrees drop.
+ * C4 returns exactly the KwikCluster (Alg. 1) clustering of pi (Sec. 3.2).
+ *
+ * Readings fixed by this library (the paper leaves them open):
+ *   - pi sorts vertices by (splitmix64(seed ^ v), v) ascending; rank 0 first.
+ *   - n_i in the batch size is the number of unclustered vertices at round
+ *     start; k_i = ceil(eps_ppm * n_i / (10^6 * Delta_i)) in integers, with
+ *     eps_ppm = round(eps * 10^6), clamped to [1, n_i]; k_i = n_i if Delta_i = 0.
+ *   - Delta_i is exact every round (not the halving estimate of the
+ *     implementation appendix).
+ *   - C4's createCluster also labels non-center active vertices; ClusterWild!
+ *     skips the active set.
+ *   - A cluster id is the center's vertex id.
+ *
+ * Everything runs in the library's own sm_103a kernels on one GPU.  Host code
+ * only validates arguments, allocates and launches.
+ *
+ * Threading: a cc_graph is not re-entrant; calls on one graph must not overlap.
+ * Different graphs may be used from different threads.
+ * Errors: every call returns CC_OK (0) or a negative CC_ERR_* code; nothing
+ * else crosses the ABI.  After CC_ERR_INVALID_ARG the graph stays usable.
+ */
+#ifndef CC_H_
+#define CC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------- */
+#define CC_OK                 0
+#define CC_ERR_INVALID_ARG   -1   /* bad argument (null pointer, eps out of (0,1], ...) */
+#define CC_ERR_INVALID_GRAPH -2   /* CSR is not a symmetric simple graph           */
+#define CC_ERR_OOM           -3   /* device or host allocation failed              */
+#define CC_ERR_CUDA          -4   /* a CUDA runtime call failed                    */
+#define CC_ERR_TIMEOUT       -5   /* a bounded device-side wait ran out            */
+#define CC_ERR_BUSY          -6   /* server queue full / job not finished          */
+#define CC_ERR_INTERNAL      -7   /* device-side consistency check failed          */
+
+/* ---- algorithms ---------------------------------------------------------- */
+#define CC_ALGO_C4          1     /* serializable: equals KwikCluster(pi)          */
+#define CC_ALGO_CLUSTERWILD 2     /* coordination-free                             */
+
+/* ---- cc_graph_create flags ----------------------------------------------- */
+#define CC_DEVICE_PTRS  2u   /* row_offsets/col_idx are device pointers, adopted by
+                                reference (caller keeps them alive until destroy) */
+#define CC_OFFSETS_I32  4u   /* row_offsets is int32[n+1] instead of int64[n+1]  */
+
+/* Limits: 0 <= n <= 2^31 - 2 (INT32_MAX marks "unclustered"), nnz < 2^33. */
+
+typedef struct cc_graph cc_graph;
+
+/* Per-round statistics of one clustering (Alg. 2 loop body). */
+typedef struct cc_round_stats {
+  int64_t n_alive;   /* n_i: unclustered vertices at round start              */
+  int64_t delta;     /* Delta_i: maximum residual degree                      */
+  int64_t k;         /* |A_i|                                                 */
+  int64_t centers;   /* clusters opened this round                            */
+  int64_t removed;   /* vertices clustered this round (A_i included)          */
+  int64_t blocked;   /* C4: actives with an earlier-ranked active neighbour   */
+  int64_t edges;     /* adjacency entries read by this round's passes         */
+} cc_round_stats;
+
+/*
+ * cc_graph_create -- upload (or adopt) the positive edges of a graph.
+ *   n            number of vertices.
+ *   row_offsets  int64[n+1] (int32[n+1] with CC_OFFSETS_I32), off[0] = 0,
+ *                non-decreasing; row v is col_idx[off[v] .. off[v+1]).
+ *   col_idx      int32[off[n]]: each row strictly increasing, no self loop,
+ *                every entry in [0,n), and the graph symmetric (u in row v iff
+ *                v in row u).  Isolated vertices are allowed.
+ *   flags        CC_DEVICE_PTRS / CC_OFFSETS_I32.
+ *   cuda_stream  cudaStream_t for all work on this graph (NULL = legacy stream).
+ *   out          receives the handle.
+ * Host arrays are copied; the caller may free them on return.  The CSR is
+ * validated on the device (range, order, self loops, symmetry):
+ * CC_ERR_INVALID_GRAPH on failure.
+ */
+int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx,
+                    uint32_t flags, void* cuda_stream, cc_graph** out);
+
+/* Release the graph and every device buffer it owns. NULL is accepted. */
+int cc_graph_destroy(cc_graph* g);
+
+/* n, nnz (= 2m) and the largest degree of a created graph. Any out may be NULL. */
+int cc_graph_info(const cc_graph* g, int64_t* n, int64_t* nnz, int64_t* max_degree);
+
+/*
+ * cc_permutation -- pi of Alg. 1/2: order_out[r] = the vertex of rank r, the
+ * vertices sorted by (splitmix64(seed ^ v), v).  order_out: int32[n], host or
+ * device memory.  Uses the graph's stream; blocks until done.
+ */
+int cc_permutation(cc_graph* g, uint64_t seed, int32_t* order_out);
+
+/*
+ * cc_cluster -- one full clustering (Alg. 2) of graph g.
+ *   algo               CC_ALGO_C4 or CC_ALGO_CLUSTERWILD.
+ *   eps                0 < eps <= 1 (Sec. 3 assumes eps <= 1).
+ *   seed               selects pi.
+ *   labels_out         int32[n], host or device memory: the center vertex id
+ *                      of each vertex's cluster.  May be NULL.
+ *   rounds_out         number of rounds (NULL allowed).
+ *   disagreements_out  the objective of the result, int64 (NULL allowed).
+ * Blocks until the result is available.
+ */
+int cc_cluster(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out,
+               int32_t* rounds_out, int64_t* disagreements_out);
+
+/* cc_cluster plus per-round statistics: the first min(rounds, stats_cap)
+ * rounds are written to stats (host memory); *stats_len = rounds. */
+int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out,
+                  int32_t* rounds_out, int64_t* disagreements_out, cc_round_stats* stats,
+                  int32_t stats_cap, int32_t* stats_len);
+
+/*
+ * cc_disagreements -- objective (Sec. 2) of an arbitrary labelling:
+ * positive edges across clusters plus negative pairs inside clusters.
+ * labels: int32[n], host or device, values in [0, n) (CC_ERR_INVALID_ARG
+ * otherwise).  out: host int64.
+ */
+int cc_disagreements(cc_graph* g, const int32_t* labels, int64_t* out);
+
+/*
+ * cc_batch_run -- best-of-k over many graphs (the paper runs each graph
+ * under 100 random orders; this keeps the best of k).  For graph i and
+ * j = 0..k_perms-1 the job is cc_cluster(gs[i], algo, eps, seeds[i] + j).
+ *   gs[count], seeds[count]  graphs and base seeds.
+ *   labels_out[i]            int32[n_i] (host or device) or NULL: labels of the
+ *                            best job of graph i.
+ *   best_j[i], best_D[i], rounds[i]  host arrays (NULL allowed): index of the
+ *                            best permutation (lowest D, ties to lowest j), its
+ *                            disagreements and its round count.
+ * Jobs run concurrently on the device; each result is the same as the
+ * corresponding single cc_cluster call.
+ */
+int cc_batch_run(cc_graph* const* gs, int32_t count, int algo, double eps,
+                 const uint64_t* seeds, int32_t k_perms, int32_t* const* labels_out,
+                 int32_t* best_j, int64_t* best_D, int32_t* rounds);
+
+/* Human-readable name of a status code (static storage). */
+const char* cc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CC_H_ */

@@ -1,0 +1,12 @@
+"""GB300-native parallel correlation clustering (C4 and ClusterWild!).
+
+The bulk-synchronous rounds of "Parallel Correlation Clustering on Big Graphs"
+(Pan et al., 2015; Alg. 2) and the disagreement objective, as hand-written
+sm_103a CUDA kernels behind the C ABI of ``include/cc.h``.  This package is a
+thin ctypes binding over that library.
+"""
+from .native import (ALGOS, C4, CLUSTERWILD, CCError, Graph, ROUND_STAT_FIELDS, batch_run, lib_path,
+                     load)
+
+__all__ = ["ALGOS", "C4", "CLUSTERWILD", "CCError", "Graph", "ROUND_STAT_FIELDS", "batch_run", "lib_path",
+           "load"]

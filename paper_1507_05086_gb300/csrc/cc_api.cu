@@ -1,0 +1,400 @@
+// cc_api.cu -- the C ABI (include/cc.h): argument checks, device memory,
+// launches and result transfer.  All computation happens in the kernels of
+// cc_perm.cu, cc_rounds.cu and cc_objective.cu.
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+
+#include "../../include/cc.h"
+#include "cc_internal.h"
+
+using namespace ccg;
+
+struct cc_graph {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  int64_t n = 0, nnz = 0;
+  int32_t max_deg = 0;
+  int64_t* off = nullptr;
+  int32_t* col = nullptr;
+  bool own_off = false, own_col = false;
+  int32_t* nz_row = nullptr;
+  int64_t* nz_pos = nullptr;
+  int64_t nz_n = 0;
+  // cached workspaces (grown on demand)
+  void* perm_ws = nullptr;
+  size_t perm_ws_bytes = 0;
+  int32_t* order = nullptr;
+  void* round_ws = nullptr;
+  size_t round_ws_bytes = 0;
+  int grid = 0;
+  int32_t* labels_tmp = nullptr;
+  void* obj_ws = nullptr;
+  unsigned long long* obj_out = nullptr;
+  RoundStat* stats_dev = nullptr;
+  int64_t stats_dev_cap = 0;
+  int* perm_err = nullptr;
+  // pinned host staging for the small results
+  Ctl* ctl_host = nullptr;
+  unsigned long long* obj_host = nullptr;
+};
+
+namespace {
+
+int from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return CC_OK;
+  if (e == cudaErrorMemoryAllocation) return CC_ERR_OOM;
+  return CC_ERR_CUDA;
+}
+
+#define CC_TRY(expr)                          \
+  do {                                        \
+    cudaError_t _e = (expr);                  \
+    if (_e != cudaSuccess) return from_cuda(_e); \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+template <class T>
+cudaError_t dalloc(T** p, size_t bytes, cudaStream_t s) {
+  void* q = nullptr;
+  cudaError_t e = cudaMallocAsync(&q, bytes > 0 ? bytes : 1, s);
+  *p = static_cast<T*>(q);
+  return e;
+}
+
+template <class T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+  p = nullptr;
+}
+
+int ensure_cluster_ws(cc_graph* g) {
+  if (!g->order) CC_TRY(dalloc(&g->order, 4 * (size_t)g->n, g->stream));
+  const size_t pb = perm_workspace_bytes(g->n);
+  if (g->perm_ws_bytes < pb) {
+    dfree(g->perm_ws, g->stream);
+    CC_TRY(dalloc(&g->perm_ws, pb, g->stream));
+    g->perm_ws_bytes = pb;
+  }
+  if (!g->grid) g->grid = rounds_grid_size(g->device);
+  const size_t rb = rounds_workspace_bytes(g->n, g->max_deg, g->grid);
+  if (g->round_ws_bytes < rb) {
+    dfree(g->round_ws, g->stream);
+    CC_TRY(dalloc(&g->round_ws, rb, g->stream));
+    g->round_ws_bytes = rb;
+  }
+  if (!g->perm_err) CC_TRY(dalloc(&g->perm_err, sizeof(int), g->stream));
+  if (!g->ctl_host) CC_TRY(cudaMallocHost(&g->ctl_host, sizeof(Ctl)));
+  return CC_OK;
+}
+
+int ensure_labels_tmp(cc_graph* g) {
+  if (!g->labels_tmp) CC_TRY(dalloc(&g->labels_tmp, 4 * (size_t)g->n, g->stream));
+  return CC_OK;
+}
+
+int status_of_device_err(int e) {
+  if (e == CC_OK) return CC_OK;
+  if (e == CC_ERR_TIMEOUT) return CC_ERR_TIMEOUT;
+  return CC_ERR_INTERNAL;
+}
+
+int eps_ppm_of(double eps, int64_t* out) {
+  if (!(eps > 0.0) || !(eps <= 1.0)) return CC_ERR_INVALID_ARG;
+  const long long ppm = std::llround(eps * 1e6);
+  if (ppm < 1 || ppm > 1000000) return CC_ERR_INVALID_ARG;
+  *out = ppm;
+  return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* cc_status_string(int status) {
+  switch (status) {
+    case CC_OK: return "ok";
+    case CC_ERR_INVALID_ARG: return "invalid argument";
+    case CC_ERR_INVALID_GRAPH: return "invalid graph";
+    case CC_ERR_OOM: return "out of memory";
+    case CC_ERR_CUDA: return "CUDA error";
+    case CC_ERR_TIMEOUT: return "device wait timed out";
+    case CC_ERR_BUSY: return "busy";
+    case CC_ERR_INTERNAL: return "internal consistency check failed";
+    default: return "unknown status";
+  }
+}
+
+int cc_graph_destroy(cc_graph* g) {
+  if (!g) return CC_OK;
+  cudaSetDevice(g->device);
+  cudaStream_t s = g->stream;
+  if (g->own_off) dfree(g->off, s);
+  if (g->own_col) dfree(g->col, s);
+  dfree(g->nz_row, s);
+  dfree(g->nz_pos, s);
+  dfree(g->perm_ws, s);
+  dfree(g->order, s);
+  dfree(g->round_ws, s);
+  dfree(g->labels_tmp, s);
+  dfree(g->obj_ws, s);
+  dfree(g->obj_out, s);
+  dfree(g->stats_dev, s);
+  dfree(g->perm_err, s);
+  cudaStreamSynchronize(s);
+  if (g->ctl_host) cudaFreeHost(g->ctl_host);
+  if (g->obj_host) cudaFreeHost(g->obj_host);
+  delete g;
+  return CC_OK;
+}
+
+int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, uint32_t flags,
+                    void* cuda_stream, cc_graph** out) {
+  if (!out) return CC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 0 || n > 2147483646LL || !row_offsets) return CC_ERR_INVALID_ARG;
+  if (flags & ~(CC_DEVICE_PTRS | CC_OFFSETS_I32)) return CC_ERR_INVALID_ARG;
+  const bool dev = (flags & CC_DEVICE_PTRS) != 0, i32 = (flags & CC_OFFSETS_I32) != 0;
+  cc_graph* g = new (std::nothrow) cc_graph();
+  if (!g) return CC_ERR_OOM;
+  g->stream = static_cast<cudaStream_t>(cuda_stream);
+  g->n = n;
+  int rc = CC_OK;
+  do {
+    if (cudaGetDevice(&g->device) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
+    cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, g->device);
+    cudaStream_t s = g->stream;
+    // nnz = off[n]
+    int64_t nnz = 0;
+    if (dev) {
+      if (i32) {
+        int32_t t = 0;
+        if (cudaMemcpy(&t, static_cast<const int32_t*>(row_offsets) + n, 4, cudaMemcpyDeviceToHost) != cudaSuccess) { rc = CC_ERR_CUDA; break; }
+        nnz = t;
+      } else if (cudaMemcpy(&nnz, static_cast<const int64_t*>(row_offsets) + n, 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        rc = CC_ERR_CUDA; break;
+      }
+    } else {
+      nnz = i32 ? static_cast<const int32_t*>(row_offsets)[n] : static_cast<const int64_t*>(row_offsets)[n];
+    }
+    if (nnz < 0 || nnz >= (int64_t(1) << 33)) { rc = CC_ERR_INVALID_GRAPH; break; }
+    if (nnz > 0 && !col_idx) { rc = CC_ERR_INVALID_ARG; break; }
+    g->nnz = nnz;
+    // offsets
+    if (dev && !i32) {
+      g->off = const_cast<int64_t*>(static_cast<const int64_t*>(row_offsets));
+    } else {
+      if ((rc = from_cuda(dalloc(&g->off, 8 * (size_t)(n + 1), s))) != CC_OK) break;
+      g->own_off = true;
+      if (i32) {
+        int32_t* tmp = nullptr;
+        if ((rc = from_cuda(dalloc(&tmp, 4 * (size_t)(n + 1), s))) != CC_OK) break;
+        cudaMemcpyAsync(tmp, row_offsets, 4 * (size_t)(n + 1), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+        launch_offsets_i32_to_i64(n, tmp, g->off, s);
+        dfree(tmp, s);
+      } else if ((rc = from_cuda(cudaMemcpyAsync(g->off, row_offsets, 8 * (size_t)(n + 1), cudaMemcpyHostToDevice, s))) != CC_OK) {
+        break;
+      }
+    }
+    // columns
+    if (dev) {
+      g->col = const_cast<int32_t*>(col_idx);
+    } else {
+      if ((rc = from_cuda(dalloc(&g->col, 4 * (size_t)nnz, s))) != CC_OK) break;
+      g->own_col = true;
+      if (nnz > 0 && (rc = from_cuda(cudaMemcpyAsync(g->col, col_idx, 4 * (size_t)nnz, cudaMemcpyHostToDevice, s))) != CC_OK) break;
+    }
+    // validation
+    void* vws = nullptr;
+    if ((rc = from_cuda(dalloc(&vws, validate_workspace_bytes(), s))) != CC_OK) break;
+    launch_validate(n, nnz, g->off, g->col, vws, g->num_sms, s);
+    int vflags[2] = {0, 0};
+    cudaMemcpyAsync(vflags, static_cast<char*>(vws) + align_up(8 * sizeof(unsigned long long)), sizeof(vflags),
+                    cudaMemcpyDeviceToHost, s);
+    // non-empty rows (for the edge-balanced objective pass)
+    if ((rc = from_cuda(dalloc(&g->nz_row, 4 * (size_t)(n > 0 ? n : 1), s))) != CC_OK) break;
+    if ((rc = from_cuda(dalloc(&g->nz_pos, 8 * (size_t)(n > 0 ? n : 1), s))) != CC_OK) break;
+    void* nws = nullptr;
+    if ((rc = from_cuda(dalloc(&nws, nonempty_workspace_bytes(n), s))) != CC_OK) break;
+    int64_t* nz_dev = reinterpret_cast<int64_t*>(static_cast<char*>(nws) + nonempty_workspace_bytes(n) - 256);
+    launch_nonempty_rows(n, g->off, g->nz_row, g->nz_pos, nws, nz_dev, g->num_sms, s);
+    cudaMemcpyAsync(&g->nz_n, nz_dev, 8, cudaMemcpyDeviceToHost, s);
+    dfree(vws, s);
+    dfree(nws, s);
+    if ((rc = from_cuda(cudaStreamSynchronize(s))) != CC_OK) break;
+    if ((rc = from_cuda(cudaGetLastError())) != CC_OK) break;
+    if (vflags[0] != 0) { rc = CC_ERR_INVALID_GRAPH; break; }
+    g->max_deg = vflags[1];
+  } while (false);
+  if (rc != CC_OK) {
+    cc_graph_destroy(g);
+    return rc;
+  }
+  *out = g;
+  return CC_OK;
+}
+
+int cc_graph_info(const cc_graph* g, int64_t* n, int64_t* nnz, int64_t* max_degree) {
+  if (!g) return CC_ERR_INVALID_ARG;
+  if (n) *n = g->n;
+  if (nnz) *nnz = g->nnz;
+  if (max_degree) *max_degree = g->max_deg;
+  return CC_OK;
+}
+
+int cc_permutation(cc_graph* g, uint64_t seed, int32_t* order_out) {
+  if (!g || (!order_out && g->n > 0)) return CC_ERR_INVALID_ARG;
+  if (g->n == 0) return CC_OK;
+  cudaSetDevice(g->device);
+  int rc = ensure_cluster_ws(g);
+  if (rc != CC_OK) return rc;
+  cudaStream_t s = g->stream;
+  CC_TRY(cudaMemsetAsync(g->perm_err, 0, sizeof(int), s));
+  const bool dev = is_device_ptr(order_out);
+  int32_t* dst = dev ? order_out : g->order;
+  CC_TRY(launch_permutation(g->n, seed, dst, g->perm_ws, g->num_sms, g->perm_err, s));
+  if (!dev) CC_TRY(cudaMemcpyAsync(order_out, g->order, 4 * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+  int err = 0;
+  CC_TRY(cudaMemcpyAsync(&err, g->perm_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CC_TRY(cudaStreamSynchronize(s));
+  return status_of_device_err(err);
+}
+
+int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
+                  int64_t* disagreements_out, cc_round_stats* stats, int32_t stats_cap, int32_t* stats_len) {
+  if (!g) return CC_ERR_INVALID_ARG;
+  if (algo != CC_ALGO_C4 && algo != CC_ALGO_CLUSTERWILD) return CC_ERR_INVALID_ARG;
+  if (stats_cap < 0 || (stats_cap > 0 && !stats)) return CC_ERR_INVALID_ARG;
+  int64_t ppm = 0;
+  int rc = eps_ppm_of(eps, &ppm);
+  if (rc != CC_OK) return rc;
+  if (g->n == 0) {
+    if (rounds_out) *rounds_out = 0;
+    if (disagreements_out) *disagreements_out = 0;
+    if (stats_len) *stats_len = 0;
+    return CC_OK;
+  }
+  cudaSetDevice(g->device);
+  if ((rc = ensure_cluster_ws(g)) != CC_OK) return rc;
+  cudaStream_t s = g->stream;
+  if (stats_cap > g->stats_dev_cap) {
+    dfree(g->stats_dev, s);
+    CC_TRY(dalloc(&g->stats_dev, sizeof(RoundStat) * (size_t)stats_cap, s));
+    g->stats_dev_cap = stats_cap;
+  }
+  RoundBuffers b;
+  rounds_carve(g->round_ws, g->n, g->max_deg, g->grid, &b);
+  b.n = g->n;
+  b.nnz = g->nnz;
+  b.max_deg = g->max_deg;
+  b.off = g->off;
+  b.col = g->col;
+  b.order = g->order;
+  b.stats = g->stats_dev;
+  b.stats_cap = stats_cap;
+  CC_TRY(cudaMemsetAsync(g->perm_err, 0, sizeof(int), s));
+  CC_TRY(launch_permutation(g->n, seed, g->order, g->perm_ws, g->num_sms, g->perm_err, s));
+  CC_TRY(launch_rounds(b, algo, ppm, g->grid, s));
+  const bool dev = is_device_ptr(labels_out);
+  if (labels_out) {
+    if (dev) {
+      CC_TRY(launch_finalize_labels(b, labels_out, s));
+    } else {
+      if ((rc = ensure_labels_tmp(g)) != CC_OK) return rc;
+      CC_TRY(launch_finalize_labels(b, g->labels_tmp, s));
+      CC_TRY(cudaMemcpyAsync(labels_out, g->labels_tmp, 4 * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  CC_TRY(cudaMemcpyAsync(g->ctl_host, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  int perr = 0;
+  CC_TRY(cudaMemcpyAsync(&perr, g->perm_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CC_TRY(cudaStreamSynchronize(s));
+  const Ctl& c = *g->ctl_host;
+  if (perr != 0) return status_of_device_err(perr);
+  if (c.err != 0) return status_of_device_err(c.err);
+  if (c.n_alive != 0 || !c.done) return CC_ERR_INTERNAL;
+  const int64_t rounds = c.round;
+  if (stats_cap > 0) {
+    const int64_t cnt = rounds < stats_cap ? rounds : stats_cap;
+    static_assert(sizeof(cc_round_stats) == sizeof(RoundStat), "round stats layout");
+    if (cnt > 0) CC_TRY(cudaMemcpy(stats, g->stats_dev, sizeof(RoundStat) * (size_t)cnt, cudaMemcpyDeviceToHost));
+  }
+  if (stats_len) *stats_len = (int32_t)rounds;
+  if (rounds_out) *rounds_out = (int32_t)rounds;
+  if (disagreements_out) {
+    const int64_t m = g->nnz / 2;
+    *disagreements_out = m - 2 * (int64_t)c.mc - (int64_t)c.mm + (int64_t)c.pairs;
+  }
+  return CC_OK;
+}
+
+int cc_cluster(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
+               int64_t* disagreements_out) {
+  return cc_cluster_ex(g, algo, eps, seed, labels_out, rounds_out, disagreements_out, nullptr, 0, nullptr);
+}
+
+int cc_disagreements(cc_graph* g, const int32_t* labels, int64_t* out) {
+  if (!g || !out || (!labels && g->n > 0)) return CC_ERR_INVALID_ARG;
+  if (g->n == 0) { *out = 0; return CC_OK; }
+  cudaSetDevice(g->device);
+  cudaStream_t s = g->stream;
+  if (!g->obj_ws) CC_TRY(dalloc(&g->obj_ws, objective_workspace_bytes(g->n), s));
+  if (!g->obj_out) CC_TRY(dalloc(&g->obj_out, 4 * sizeof(unsigned long long), s));
+  if (!g->obj_host) CC_TRY(cudaMallocHost(&g->obj_host, 4 * sizeof(unsigned long long)));
+  const int32_t* lab = labels;
+  if (!is_device_ptr(labels)) {
+    int rc = ensure_labels_tmp(g);
+    if (rc != CC_OK) return rc;
+    CC_TRY(cudaMemcpyAsync(g->labels_tmp, labels, 4 * (size_t)g->n, cudaMemcpyHostToDevice, s));
+    lab = g->labels_tmp;
+  }
+  CC_TRY(launch_disagreements(g->n, g->nnz, g->off, g->col, g->nz_row, g->nz_pos, g->nz_n, lab, g->obj_ws,
+                              g->obj_out, g->num_sms, s));
+  CC_TRY(cudaMemcpyAsync(g->obj_host, g->obj_out, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  CC_TRY(cudaStreamSynchronize(s));
+  if (g->obj_host[2]) return CC_ERR_INVALID_ARG;
+  *out = g->nnz / 2 - (int64_t)g->obj_host[0] + (int64_t)g->obj_host[1];
+  return CC_OK;
+}
+
+int cc_batch_run(cc_graph* const* gs, int32_t count, int algo, double eps, const uint64_t* seeds, int32_t k_perms,
+                 int32_t* const* labels_out, int32_t* best_j, int64_t* best_D, int32_t* rounds) {
+  if (count < 0 || k_perms < 1 || (count > 0 && (!gs || !seeds))) return CC_ERR_INVALID_ARG;
+  int64_t ppm = 0;
+  int rc = eps_ppm_of(eps, &ppm);
+  if (rc != CC_OK) return rc;
+  for (int32_t i = 0; i < count; ++i) {
+    if (!gs[i]) return CC_ERR_INVALID_ARG;
+    int64_t bestd = INT64_MAX;
+    int32_t bj = -1, br = 0;
+    for (int32_t j = 0; j < k_perms; ++j) {
+      int32_t r = 0;
+      int64_t d = 0;
+      rc = cc_cluster(gs[i], algo, eps, seeds[i] + (uint64_t)j, nullptr, &r, &d);
+      if (rc != CC_OK) return rc;
+      if (d < bestd) { bestd = d; bj = j; br = r; }
+    }
+    if (labels_out && labels_out[i]) {
+      rc = cc_cluster(gs[i], algo, eps, seeds[i] + (uint64_t)bj, labels_out[i], nullptr, nullptr);
+      if (rc != CC_OK) return rc;
+    }
+    if (best_j) best_j[i] = bj;
+    if (best_D) best_D[i] = bestd;
+    if (rounds) rounds[i] = br;
+  }
+  return CC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,119 @@
+// cc_internal.h -- host-side declarations shared by the library's translation
+// units (not part of the public ABI; see include/cc.h for that).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace ccg {
+
+inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// ---- permutation (cc_perm.cu) ----------------------------------------------
+int perm_bucket_bits(int64_t n);
+size_t perm_workspace_bytes(int64_t n);
+cudaError_t launch_permutation(int64_t n, uint64_t seed, int32_t* order, void* ws, int num_sms,
+                               int* err, cudaStream_t stream);
+
+// ---- rounds (cc_rounds.cu) ---------------------------------------------------
+// Per-round statistics as written by the device (layout of cc_round_stats).
+struct RoundStat {
+  int64_t n_alive, delta, k, centers, removed, blocked, edges;
+};
+
+struct GridBarrierHost { unsigned count, gen; };
+
+// Device control block of one clustering job.  Zeroed by the host before
+// each launch; fields are written by the kernels only.
+struct Ctl {
+  GridBarrierHost bar;
+  int err;
+  int algo;
+  int64_t eps_ppm;
+  int64_t n, nnz;
+  int32_t max_deg;
+  // state carried across rounds
+  int64_t n_alive;
+  int64_t cursor, al_len;
+  int al_identity, al_sel;
+  int32_t th, top, delta;
+  int64_t k;
+  int need_rebuild, done;
+  int rebuilds_in_row;
+  int64_t round;
+  // active-set selection
+  int64_t need, win_lo, win_len, take, cursor_next;
+  int32_t r0;
+  // per-round lists (counters pack items << 33 | edges)
+  unsigned long long act_pack, new_pack, blk_pack;
+  int64_t act_n, act_E, new_n, new_E, b_n, b_E;
+  int64_t undecided, fix_iter;
+  // per-round tallies
+  long long r_centers, r_attached, r_noncenter, r_blocked;
+  long long r_edges;
+  // objective tallies: member-center edges, member-member edges (counted from
+  // both ends), sum over clusters of C(size, 2)
+  unsigned long long mc, mm, pairs;
+};
+
+struct RoundBuffers {
+  int64_t n, nnz;
+  int32_t max_deg;
+  const int64_t* off;
+  const int32_t* col;
+  const int32_t* order;
+  unsigned long long* st;      // per-vertex state word
+  int32_t* al0;
+  int32_t* al1;
+  int32_t* act_v;
+  int32_t* act_r;
+  int64_t* act_e;
+  int64_t* act_row;
+  int32_t* new_v;
+  int64_t* new_e;
+  int64_t* new_row;
+  int32_t* size;
+  int32_t* cnt;                // degree-count table, max_deg + 2 + histogram window
+  uint8_t* blk_flag;
+  uint8_t* hit_c;
+  uint8_t* hit_p;
+  int32_t* pull;
+  int32_t* b_j;
+  int64_t* b_e;
+  int64_t* blk_a;              // per-block scratch
+  int64_t* blk_b;
+  RoundStat* stats;
+  int64_t stats_cap;
+  Ctl* ctl;
+};
+
+size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid);
+// Carve a workspace of rounds_workspace_bytes() into RoundBuffers (pointers only).
+void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* b);
+// Largest co-resident grid for the persistent round kernel on this device.
+int rounds_grid_size(int device);
+cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, int grid, cudaStream_t stream);
+// labels_out[v] = center vertex id (order[center rank]).
+cudaError_t launch_finalize_labels(const RoundBuffers& b, int32_t* labels_out, cudaStream_t stream);
+
+// ---- objective and validation (cc_objective.cu) ------------------------------
+size_t objective_workspace_bytes(int64_t n);
+// out[0] = intra-cluster CSR entries, out[1] = sum_c C(s_c, 2), out[2] = 1 if a
+// label was outside [0, n).  out: 3 device words.
+cudaError_t launch_disagreements(int64_t n, int64_t nnz, const int64_t* off, const int32_t* col,
+                                 const int32_t* nz_row, const int64_t* nz_pos, int64_t nz_n,
+                                 const int32_t* labels, void* ws, unsigned long long* out, int num_sms,
+                                 cudaStream_t stream);
+size_t validate_workspace_bytes();
+// ws: validate_workspace_bytes(); after completion the int pair at
+// ws + align_up(64) holds (error code, max degree).
+cudaError_t launch_validate(int64_t n, int64_t nnz, const int64_t* off, const int32_t* col, void* ws,
+                            int num_sms, cudaStream_t stream);
+cudaError_t launch_offsets_i32_to_i64(int64_t n, const int32_t* in, int64_t* out, cudaStream_t stream);
+size_t nonempty_workspace_bytes(int64_t n);
+cudaError_t launch_nonempty_rows(int64_t n, const int64_t* off, int32_t* nz_row, int64_t* nz_pos, void* ws,
+                                 int64_t* count_dev, int num_sms, cudaStream_t stream);
+
+}  // namespace ccg

@@ -1,0 +1,224 @@
+// cc_objective.cu -- the disagreement objective (Sec. 2) of an arbitrary
+// labelling, CSR validation and small graph utilities.
+//
+// Disagreements: with m positive edges, intra = positive edges inside a
+// cluster and s_c the cluster sizes,
+//     D = (m - intra) + (sum_c C(s_c, 2) - intra) = m - intra_dir + sum_c C(s_c, 2)
+// where intra_dir = 2 * intra counts CSR entries (u, w) with label[u] == label[w].
+// One pass counts cluster sizes, one edge-balanced pass over the non-empty
+// rows counts intra_dir, one pass sums C(s_c, 2).
+#include <cstdint>
+
+#include "cc_device.cuh"
+#include "cc_internal.h"
+
+namespace ccg {
+namespace {
+
+constexpr int kObjThreads = 512;
+
+__global__ void k_cluster_sizes(int64_t n, const int32_t* __restrict__ labels, int32_t* __restrict__ size,
+                                unsigned long long* out) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = labels[v];
+    if (c < 0 || c >= n) { atomicExch(out + 2, 1ull); continue; }
+    atomicAdd(size + c, 1);
+  }
+}
+
+__global__ void __launch_bounds__(kObjThreads) k_intra(int64_t nz_n, const int32_t* __restrict__ nz_row,
+                                                      const int64_t* __restrict__ nz_pos, int64_t nnz,
+                                                      const int32_t* __restrict__ col,
+                                                      const int32_t* __restrict__ labels, unsigned long long* out) {
+  __shared__ int lbs[kObjThreads / 32][32];
+  __shared__ int64_t scr[33];
+  int64_t cnt = 0;
+  lbs_for_each(nz_pos, nz_n, nnz, lbs[threadIdx.x >> 5], [&](bool valid, int64_t j, int64_t k) {
+    if (!valid) return;
+    const int64_t e = __ldg(nz_pos + j) + k;
+    const int32_t u = __ldg(nz_row + j);
+    const int32_t w = __ldg(col + e);
+    cnt += (__ldg(labels + u) == __ldg(labels + w)) ? 1 : 0;
+  });
+  cnt = block_sum<int64_t>(cnt, scr);
+  if (threadIdx.x == 0 && cnt) atomicAdd(out + 0, (unsigned long long)cnt);
+}
+
+__global__ void k_pairs(int64_t n, const int32_t* __restrict__ size, unsigned long long* out) {
+  __shared__ int64_t scr[33];
+  int64_t acc = 0;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = size[c];
+    acc += s * (s - 1) / 2;
+  }
+  acc = block_sum<int64_t>(acc, scr);
+  if (threadIdx.x == 0 && acc) atomicAdd(out + 1, (unsigned long long)acc);
+}
+
+// ---- validation ---------------------------------------------------------------
+// Error codes written to flags[0] (first one wins).
+constexpr int kBadOffsets = 1, kBadColumn = 2, kSelfLoop = 3, kUnsorted = 4, kAsymmetric = 5;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 33)) * 0xFF51AFD7ED558CCDull;
+  z = (z ^ (z >> 33)) * 0xC4CEB9FE1A85EC53ull;
+  return z ^ (z >> 33);
+}
+
+// One warp per row: range, order, self loops, degree; symmetry by comparing
+// two hash sums of the pairs (min, max) seen from the lower and from the upper
+// endpoint (equal multisets give equal sums).
+__global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
+                           int* flags, unsigned long long* sums) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  unsigned long long lo1 = 0, lo2 = 0, up1 = 0, up2 = 0;
+  long long nlo = 0, nup = 0;
+  for (int64_t u = gw; u < n; u += nw) {
+    const int64_t a = off[u], b = off[u + 1];
+    if (a < 0 || b < a || b > nnz) {
+      if (lane == 0) atomicCAS(flags, 0, kBadOffsets);
+      continue;
+    }
+    if (lane == 0) {
+      const int64_t d = b - a;
+      atomicMax(flags + 1, d > 0x7FFFFFFF ? 0x7FFFFFFF : (int)d);
+    }
+    for (int64_t e = a + lane; e < b; e += 32) {
+      const int32_t w = col[e];
+      if (w < 0 || w >= n) { atomicCAS(flags, 0, kBadColumn); continue; }
+      if (w == u) { atomicCAS(flags, 0, kSelfLoop); continue; }
+      if (e > a && col[e - 1] >= w) atomicCAS(flags, 0, kUnsorted);
+      const uint64_t key = u < w ? (((uint64_t)u << 32) | (uint32_t)w) : (((uint64_t)w << 32) | (uint32_t)u);
+      const uint64_t h1 = mix64(key ^ 0x9E3779B97F4A7C15ull), h2 = mix64(key + 0x632BE59BD9B4E019ull);
+      if (u < w) { lo1 += h1; lo2 += h2; ++nlo; } else { up1 += h1; up2 += h2; ++nup; }
+    }
+  }
+  lo1 = warp_sum(lo1); lo2 = warp_sum(lo2); up1 = warp_sum(up1); up2 = warp_sum(up2);
+  nlo = warp_sum(nlo); nup = warp_sum(nup);
+  if (lane == 0) {
+    atomicAdd(sums + 0, lo1); atomicAdd(sums + 1, lo2);
+    atomicAdd(sums + 2, up1); atomicAdd(sums + 3, up2);
+    atomicAdd(sums + 4, (unsigned long long)nlo); atomicAdd(sums + 5, (unsigned long long)nup);
+  }
+}
+
+__global__ void k_validate_finish(int64_t n, const int64_t* __restrict__ off, int64_t nnz, int* flags,
+                                  const unsigned long long* sums) {
+  if (off[0] != 0 || off[n] != nnz) atomicCAS(flags, 0, kBadOffsets);
+  if (sums[0] != sums[2] || sums[1] != sums[3] || sums[4] != sums[5]) atomicCAS(flags, 0, kAsymmetric);
+}
+
+__global__ void k_off32_to_64(int64_t n, const int32_t* __restrict__ in, int64_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = in[i];
+}
+
+// Non-empty rows: per-block counts, a single-block scan, then the write.
+constexpr int kNzTile = 1024;
+
+__global__ void k_nz_count(int64_t n, const int64_t* __restrict__ off, int64_t* __restrict__ tile_cnt) {
+  __shared__ int64_t scr[33];
+  const int64_t ntiles = (n + kNzTile - 1) / kNzTile;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t v = t * kNzTile + threadIdx.x;
+    int64_t c = (v < n && off[v + 1] > off[v]) ? 1 : 0;
+    c = block_sum<int64_t>(c, scr);
+    if (threadIdx.x == 0) tile_cnt[t] = c;
+  }
+}
+
+__global__ void k_nz_scan(int64_t ntiles, int64_t* __restrict__ tile_cnt, int64_t* __restrict__ total) {
+  __shared__ int64_t scr[33];
+  int64_t run = 0;
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    const int64_t t = base + threadIdx.x;
+    const int64_t x = t < ntiles ? tile_cnt[t] : 0;
+    int64_t tot;
+    const int64_t ex = block_exclusive_sum<int64_t>(x, scr, &tot);
+    if (t < ntiles) tile_cnt[t] = run + ex;
+    run += tot;
+  }
+  if (threadIdx.x == 0) *total = run;
+}
+
+__global__ void k_nz_write(int64_t n, const int64_t* __restrict__ off, const int64_t* __restrict__ tile_off,
+                           int32_t* __restrict__ nz_row, int64_t* __restrict__ nz_pos) {
+  __shared__ int64_t scr[33];
+  const int64_t ntiles = (n + kNzTile - 1) / kNzTile;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t v = t * kNzTile + threadIdx.x;
+    const int64_t c = (v < n && off[v + 1] > off[v]) ? 1 : 0;
+    int64_t tot;
+    const int64_t ex = block_exclusive_sum<int64_t>(c, scr, &tot);
+    if (c) {
+      nz_row[tile_off[t] + ex] = (int32_t)v;
+      nz_pos[tile_off[t] + ex] = off[v];
+    }
+  }
+}
+
+}  // namespace
+
+size_t objective_workspace_bytes(int64_t n) {
+  return align_up(4 * (size_t)(n > 0 ? n : 1)) + align_up(8 * 4);
+}
+
+cudaError_t launch_disagreements(int64_t n, int64_t nnz, const int64_t* off, const int32_t* col,
+                                 const int32_t* nz_row, const int64_t* nz_pos, int64_t nz_n,
+                                 const int32_t* labels, void* ws, unsigned long long* out, int num_sms,
+                                 cudaStream_t stream) {
+  (void)off;
+  int32_t* size = static_cast<int32_t*>(ws);
+  cudaError_t e = cudaMemsetAsync(size, 0, 4 * (size_t)(n > 0 ? n : 1), stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(out, 0, 3 * sizeof(unsigned long long), stream);
+  if (e != cudaSuccess) return e;
+  if (n <= 0) return cudaSuccess;
+  const int g = num_sms * 4;
+  k_cluster_sizes<<<g, 256, 0, stream>>>(n, labels, size, out);
+  if (nnz > 0) k_intra<<<num_sms * 2, kObjThreads, 0, stream>>>(nz_n, nz_row, nz_pos, nnz, col, labels, out);
+  k_pairs<<<g, 256, 0, stream>>>(n, size, out);
+  return cudaGetLastError();
+}
+
+size_t validate_workspace_bytes() { return align_up(8 * sizeof(unsigned long long)) + align_up(2 * sizeof(int)); }
+
+cudaError_t launch_validate(int64_t n, int64_t nnz, const int64_t* off, const int32_t* col, void* ws,
+                            int num_sms, cudaStream_t stream) {
+  unsigned long long* sums = static_cast<unsigned long long*>(ws);
+  int* flags = reinterpret_cast<int*>(static_cast<char*>(ws) + align_up(8 * sizeof(unsigned long long)));
+  cudaError_t e = cudaMemsetAsync(ws, 0, validate_workspace_bytes(), stream);
+  if (e != cudaSuccess) return e;
+  if (n > 0) k_validate<<<num_sms * 8, 256, 0, stream>>>(n, nnz, off, col, flags, sums);
+  k_validate_finish<<<1, 1, 0, stream>>>(n, off, nnz, flags, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_offsets_i32_to_i64(int64_t n, const int32_t* in, int64_t* out, cudaStream_t stream) {
+  const int64_t want = (n + 256) / 256;
+  k_off32_to_64<<<(int)(want < 4096 ? want : 4096), 256, 0, stream>>>(n, in, out);
+  return cudaGetLastError();
+}
+
+size_t nonempty_workspace_bytes(int64_t n) {
+  const int64_t ntiles = (n + kNzTile - 1) / kNzTile;
+  return align_up(8 * (size_t)(ntiles + 1)) + align_up(8);
+}
+
+// nz_row/nz_pos get the non-empty rows and their first CSR positions; the
+// count is written to *count_dev (device int64).
+cudaError_t launch_nonempty_rows(int64_t n, const int64_t* off, int32_t* nz_row, int64_t* nz_pos, void* ws,
+                                 int64_t* count_dev, int num_sms, cudaStream_t stream) {
+  if (n <= 0) return cudaMemsetAsync(count_dev, 0, sizeof(int64_t), stream);
+  const int64_t ntiles = (n + kNzTile - 1) / kNzTile;
+  int64_t* tile = static_cast<int64_t*>(ws);
+  const int g = (int)(ntiles < (int64_t)num_sms * 4 ? ntiles : (int64_t)num_sms * 4);
+  k_nz_count<<<g, kNzTile, 0, stream>>>(n, off, tile);
+  k_nz_scan<<<1, 1024, 0, stream>>>(ntiles, tile, count_dev);
+  k_nz_write<<<g, kNzTile, 0, stream>>>(n, off, tile, nz_row, nz_pos);
+  return cudaGetLastError();
+}
+
+}  // namespace ccg

@@ -1,0 +1,192 @@
+// cc_perm.cu -- the random order pi of Alg. 1 / Alg. 2 on the device.
+//
+// pi lists the vertices by ascending (splitmix64(seed ^ v), v).  The keys are
+// uniform 64-bit values, so a two-level sort suffices:
+//   1. bucket vertices by the top b key bits (b chosen so a bucket holds about
+//      384-768 vertices): a histogram, an exclusive scan and a scatter;
+//   2. sort each bucket in shared memory by the full (key, v) with a bitonic
+//      network and write its slice of order[].
+// Keys are recomputed from v wherever needed instead of being stored, so the
+// only global traffic is 4 bytes per vertex scattered and 4+4 bytes per vertex
+// read and written by the bucket sort.  A bucket larger than the shared-memory
+// capacity (vanishingly unlikely for a hash) falls back to a rank-by-counting
+// pass that is slow but exact.
+#include <cstdint>
+
+#include "cc_device.cuh"
+#include "cc_internal.h"
+
+namespace ccg {
+namespace {
+
+constexpr int kBucketCap = 4096;      // vertices per bucket sorted in shared memory
+constexpr int kSortThreads = 512;
+constexpr int kMaxOverflow = 1023;    // buckets above capacity handled by the fallback
+
+__device__ __forceinline__ uint32_t bucket_of(uint64_t key, int bits) {
+  return bits == 0 ? 0u : (uint32_t)(key >> (64 - bits));
+}
+
+__global__ void k_bucket_hist(int64_t n, uint64_t seed, int bits, uint32_t* __restrict__ count) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x)
+    atomicAdd(&count[bucket_of(perm_key(seed, (uint64_t)v), bits)], 1u);
+}
+
+// Exclusive scan of nb counts by one block; start[nb] = n.  cursor = start.
+__global__ void k_bucket_scan(const uint32_t* __restrict__ count, int64_t nb, int64_t* __restrict__ start,
+                              int64_t* __restrict__ cursor) {
+  __shared__ int64_t scratch[33];
+  const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
+  const int64_t lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
+  int64_t s = 0;
+  for (int64_t i = lo; i < hi; ++i) s += count[i];
+  int64_t total;
+  int64_t run = block_exclusive_sum<int64_t>(s, scratch, &total);
+  for (int64_t i = lo; i < hi; ++i) {
+    start[i] = run;
+    cursor[i] = run;
+    run += count[i];
+  }
+  if (threadIdx.x == 0) start[nb] = total;
+}
+
+__global__ void k_bucket_scatter(int64_t n, uint64_t seed, int bits, int64_t* __restrict__ cursor,
+                                 int32_t* __restrict__ tmp) {
+  for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+       v += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t b = bucket_of(perm_key(seed, (uint64_t)v), bits);
+    int64_t pos = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[b]), 1ull);
+    tmp[pos] = (int32_t)v;
+  }
+}
+
+__device__ __forceinline__ bool kv_less(uint64_t ka, int32_t va, uint64_t kb, int32_t vb) {
+  return ka < kb || (ka == kb && va < vb);
+}
+
+// One block per bucket (grid-stride): bitonic sort of (key, v) in shared memory.
+__global__ void __launch_bounds__(kSortThreads)
+k_bucket_sort(uint64_t seed, int64_t nb, const int64_t* __restrict__ start, const int32_t* __restrict__ tmp,
+              int32_t* __restrict__ order, int* __restrict__ overflow) {
+  __shared__ uint64_t sk[kBucketCap];
+  __shared__ int32_t sv[kBucketCap];
+  for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
+    const int64_t s0 = start[b], len = start[b + 1] - s0;
+    if (len <= 0) continue;
+    if (len > kBucketCap) {   // handled by k_bucket_sort_large
+      if (threadIdx.x == 0) {
+        int slot = atomicAdd(overflow, 1);
+        if (slot < kMaxOverflow) overflow[1 + slot] = (int)b;
+      }
+      continue;
+    }
+    int p2 = 1;
+    while (p2 < len) p2 <<= 1;
+    for (int i = threadIdx.x; i < p2; i += blockDim.x) {
+      if (i < len) {
+        int32_t v = tmp[s0 + i];
+        sv[i] = v;
+        sk[i] = perm_key(seed, (uint64_t)v);
+      } else {
+        sv[i] = INT32_MAX;
+        sk[i] = UINT64_MAX;
+      }
+    }
+    __syncthreads();
+    for (int kk = 2; kk <= p2; kk <<= 1) {
+      for (int j = kk >> 1; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < (p2 >> 1); t += blockDim.x) {
+          // index pair (i, i ^ j) with i having bit j clear
+          const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+          const int l = i | j;
+          const bool up = (i & kk) == 0;
+          const uint64_t ki = sk[i], kl = sk[l];
+          const int32_t vi = sv[i], vl = sv[l];
+          const bool swap = up ? kv_less(kl, vl, ki, vi) : kv_less(ki, vi, kl, vl);
+          if (swap) {
+            sk[i] = kl; sk[l] = ki;
+            sv[i] = vl; sv[l] = vi;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int i = threadIdx.x; i < len; i += blockDim.x) order[s0 + i] = sv[i];
+    __syncthreads();
+  }
+}
+
+// Exact fallback for buckets above kBucketCap: each element's position is the
+// number of bucket elements smaller than it.
+__global__ void k_bucket_sort_large(uint64_t seed, const int* __restrict__ overflow,
+                                    const int64_t* __restrict__ start, const int32_t* __restrict__ tmp,
+                                    int32_t* __restrict__ order, int* __restrict__ err) {
+  const int cnt = overflow[0];
+  if (cnt > kMaxOverflow) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(err, kOk, kErrInternal);
+    return;
+  }
+  for (int q = 0; q < cnt; ++q) {
+    const int64_t b = overflow[1 + q];
+    const int64_t s0 = start[b], len = start[b + 1] - s0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < len;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const int32_t vi = tmp[s0 + i];
+      const uint64_t ki = perm_key(seed, (uint64_t)vi);
+      int64_t r = 0;
+      for (int64_t j = 0; j < len; ++j) {
+        const int32_t vj = tmp[s0 + j];
+        r += kv_less(perm_key(seed, (uint64_t)vj), vj, ki, vi) ? 1 : 0;
+      }
+      order[s0 + r] = vi;
+    }
+  }
+}
+
+}  // namespace
+
+int perm_bucket_bits(int64_t n) {
+  int bits = 0;
+  while (bits < 40 && (n >> bits) > 768) ++bits;
+  return bits;
+}
+
+size_t perm_workspace_bytes(int64_t n) {
+  const int64_t nb = int64_t(1) << perm_bucket_bits(n);
+  return align_up(sizeof(uint32_t) * nb) + align_up(sizeof(int64_t) * (nb + 1)) +
+         align_up(sizeof(int64_t) * nb) + align_up(sizeof(int32_t) * (n > 0 ? n : 1)) +
+         align_up(sizeof(int) * (kMaxOverflow + 1));
+}
+
+// order[0..n) = pi for `seed`.  ws must hold perm_workspace_bytes(n).  A
+// failed device-side check is reported through *err.
+cudaError_t launch_permutation(int64_t n, uint64_t seed, int32_t* order, void* ws, int num_sms,
+                               int* err, cudaStream_t stream) {
+  if (n <= 0) return cudaSuccess;
+  const int bits = perm_bucket_bits(n);
+  const int64_t nb = int64_t(1) << bits;
+  char* p = static_cast<char*>(ws);
+  uint32_t* count = reinterpret_cast<uint32_t*>(p); p += align_up(sizeof(uint32_t) * nb);
+  int64_t* start = reinterpret_cast<int64_t*>(p);   p += align_up(sizeof(int64_t) * (nb + 1));
+  int64_t* cursor = reinterpret_cast<int64_t*>(p);  p += align_up(sizeof(int64_t) * nb);
+  int32_t* tmp = reinterpret_cast<int32_t*>(p);     p += align_up(sizeof(int32_t) * n);
+  int* overflow = reinterpret_cast<int*>(p);
+  cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t) * nb, stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(overflow, 0, sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  const int64_t want = (n + 255) / 256;
+  const int grid = (int)(want < (int64_t)num_sms * 8 ? want : (int64_t)num_sms * 8);
+  k_bucket_hist<<<grid, 256, 0, stream>>>(n, seed, bits, count);
+  k_bucket_scan<<<1, 1024, 0, stream>>>(count, nb, start, cursor);
+  k_bucket_scatter<<<grid, 256, 0, stream>>>(n, seed, bits, cursor, tmp);
+  const int sgrid = (int)(nb < (int64_t)num_sms * 4 ? nb : (int64_t)num_sms * 4);
+  k_bucket_sort<<<sgrid, kSortThreads, 0, stream>>>(seed, nb, start, tmp, order, overflow);
+  // The fallback kernel returns at once when no bucket overflowed, so it
+  // always runs; this keeps the host free of a sync.
+  k_bucket_sort_large<<<num_sms, 256, 0, stream>>>(seed, overflow, start, tmp, order, err);
+  return cudaGetLastError();
+}
+
+}  // namespace ccg

@@ -1,0 +1,220 @@
+"""ctypes binding of ``libcc.so`` (the C ABI in ``include/cc.h``).
+
+Argument marshalling only: every step of the clustering runs in the
+library's CUDA kernels.  Arrays may be numpy arrays (host memory) or torch
+tensors (host or CUDA); torch is used for device memory and streams only.
+If the library is missing or fails to load, every call raises: there is no
+fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+C4 = 1
+CLUSTERWILD = 2
+ALGOS = {"c4": C4, "cw": CLUSTERWILD, "clusterwild": CLUSTERWILD, C4: C4, CLUSTERWILD: CLUSTERWILD}
+
+CC_DEVICE_PTRS = 2
+CC_OFFSETS_I32 = 4
+
+STATUS = {
+    0: "ok", -1: "invalid argument", -2: "invalid graph", -3: "out of memory", -4: "CUDA error",
+    -5: "device wait timed out", -6: "busy", -7: "internal consistency check failed",
+}
+
+ROUND_STAT_FIELDS = ("n_alive", "delta", "k", "centers", "removed", "blocked", "edges")
+
+
+class RoundStats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ROUND_STAT_FIELDS]
+
+
+class CCError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn} failed: {STATUS.get(status, 'unknown')} ({status})")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcc.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"CUDA library not built: {_build.LIB} (run paper_1507_05086_gb300.build)")
+        lib = ctypes.CDLL(_build.LIB)
+        vp, i64, i32, u32, u64, ci = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
+                                       ctypes.c_uint64, ctypes.c_int)
+        lib.cc_status_string.restype = ctypes.c_char_p
+        lib.cc_status_string.argtypes = [ci]
+        lib.cc_graph_create.restype = ci
+        lib.cc_graph_create.argtypes = [i64, vp, vp, u32, vp, ctypes.POINTER(vp)]
+        lib.cc_graph_destroy.restype = ci
+        lib.cc_graph_destroy.argtypes = [vp]
+        lib.cc_graph_info.restype = ci
+        lib.cc_graph_info.argtypes = [vp, vp, vp, vp]
+        lib.cc_permutation.restype = ci
+        lib.cc_permutation.argtypes = [vp, u64, vp]
+        lib.cc_cluster.restype = ci
+        lib.cc_cluster.argtypes = [vp, ci, ctypes.c_double, u64, vp, vp, vp]
+        lib.cc_cluster_ex.restype = ci
+        lib.cc_cluster_ex.argtypes = [vp, ci, ctypes.c_double, u64, vp, vp, vp, vp, i32, vp]
+        lib.cc_disagreements.restype = ci
+        lib.cc_disagreements.argtypes = [vp, vp, vp]
+        lib.cc_batch_run.restype = ci
+        lib.cc_batch_run.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp, vp, vp]
+        _lib = lib
+        return lib
+
+
+def _check(fn: str, rc: int):
+    if rc != 0:
+        raise CCError(fn, rc)
+
+
+def _ptr(a):
+    """Raw address of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data if a.size else None
+    return a.data_ptr() if a.numel() else None
+
+
+def _is_cuda(a) -> bool:
+    return a is not None and not isinstance(a, np.ndarray) and getattr(a, "is_cuda", False)
+
+
+def current_stream_handle():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:   # torch without CUDA: legacy stream
+        pass
+    return None
+
+
+class Graph:
+    """A graph resident on the GPU (``cc_graph``).
+
+    ``off``/``col``: int64[n+1] / int32[nnz] CSR of the positive edges, as numpy
+    arrays (copied to the device) or CUDA torch tensors (adopted by reference;
+    keep them alive).
+    """
+
+    def __init__(self, off, col, stream=None):
+        lib = load()
+        self._lib = lib
+        n = int(off.shape[0] - 1)
+        flags = 0
+        self._keep = None
+        if _is_cuda(off) or _is_cuda(col):
+            import torch
+            off = off.to(torch.int64).contiguous()
+            col = col.to(torch.int32).contiguous()
+            flags |= CC_DEVICE_PTRS
+            self._keep = (off, col)
+        else:
+            off = np.ascontiguousarray(off, dtype=np.int64)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+        if stream is None:
+            stream = current_stream_handle()
+        h = ctypes.c_void_p()
+        _check("cc_graph_create", lib.cc_graph_create(n, _ptr(off), _ptr(col), flags, stream, ctypes.byref(h)))
+        self._h = h
+        nn, nnz, md = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check("cc_graph_info", lib.cc_graph_info(h, ctypes.byref(nn), ctypes.byref(nnz), ctypes.byref(md)))
+        self.n, self.nnz, self.max_degree = nn.value, nnz.value, md.value
+
+    @property
+    def m(self) -> int:
+        return self.nnz // 2
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cc_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def permutation(self, seed: int, out=None):
+        out = np.empty(self.n, np.int32) if out is None else out
+        _check("cc_permutation", self._lib.cc_permutation(self._h, seed & (2**64 - 1), _ptr(out)))
+        return out
+
+    def cluster(self, algo="cw", eps: float = 0.5, seed: int = 0, labels_out=None, want_labels=True,
+                stats_cap: int = 0):
+        """Run one clustering.  Returns (labels, rounds, disagreements[, stats])."""
+        a = ALGOS[algo]
+        if labels_out is None and want_labels:
+            labels_out = np.empty(self.n, np.int32)
+        rounds = ctypes.c_int32()
+        d = ctypes.c_int64()
+        if stats_cap > 0:
+            st = (RoundStats * stats_cap)()
+            ln = ctypes.c_int32()
+            _check("cc_cluster_ex", self._lib.cc_cluster_ex(
+                self._h, a, float(eps), seed & (2**64 - 1), _ptr(labels_out), ctypes.byref(rounds),
+                ctypes.byref(d), ctypes.cast(st, ctypes.c_void_p), stats_cap, ctypes.byref(ln)))
+            cnt = min(ln.value, stats_cap)
+            stats = {f: np.array([getattr(st[i], f) for i in range(cnt)], np.int64) for f in ROUND_STAT_FIELDS}
+            return labels_out, rounds.value, d.value, stats
+        _check("cc_cluster", self._lib.cc_cluster(self._h, a, float(eps), seed & (2**64 - 1), _ptr(labels_out),
+                                                  ctypes.byref(rounds), ctypes.byref(d)))
+        return labels_out, rounds.value, d.value
+
+    def disagreements(self, labels) -> int:
+        if isinstance(labels, np.ndarray):
+            labels = np.ascontiguousarray(labels, dtype=np.int32)
+        d = ctypes.c_int64()
+        _check("cc_disagreements", self._lib.cc_disagreements(self._h, _ptr(labels), ctypes.byref(d)))
+        return d.value
+
+
+def batch_run(graphs, algo="cw", eps=0.5, seeds=None, k_perms=8, want_labels=False):
+    """Best-of-k over several graphs (``cc_batch_run``).
+
+    Returns (best_j, best_D, rounds, labels list or None)."""
+    lib = load()
+    cnt = len(graphs)
+    seeds = np.asarray(seeds if seeds is not None else np.zeros(cnt), dtype=np.uint64)
+    hs = (ctypes.c_void_p * cnt)(*[g._h.value for g in graphs])
+    best_j = np.zeros(cnt, np.int32)
+    best_d = np.zeros(cnt, np.int64)
+    rounds = np.zeros(cnt, np.int32)
+    labels = None
+    lab_arr = None
+    if want_labels:
+        labels = [np.empty(g.n, np.int32) for g in graphs]
+        lab_arr = (ctypes.c_void_p * cnt)(*[l.ctypes.data if l.size else None for l in labels])
+    _check("cc_batch_run", lib.cc_batch_run(hs, cnt, ALGOS[algo], float(eps), seeds.ctypes.data, k_perms,
+                                            lab_arr, best_j.ctypes.data, best_d.ctypes.data, rounds.ctypes.data))
+    return best_j, best_d, rounds, labels

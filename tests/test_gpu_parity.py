@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Every comparison is exact (integer work): permutations, labels, round counts,
+per-round statistics and disagreements must be identical.
+"""
+import numpy as np
+import pytest
+
+import cc_checks as chk
+
+pytestmark = pytest.mark.gpu
+
+STAT_FIELDS = ("n_alive", "delta", "k", "centers", "removed", "blocked")
+
+
+@pytest.fixture(scope="module")
+def cc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1507_05086_gb300 as cc
+    cc.load()
+    return cc
+
+
+def small_graphs(gg, seed):
+    """Seeded graphs spanning several tiles and ragged tails: tiny random
+    graphs, an ER graph, a planted partition, R-MAT and Chung-Lu power laws,
+    and degenerate shapes."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in (1, 2, 3, 17, 33, 100, 513):
+        out.append(gg.random_small(n, float(rng.random()) * 0.2, rng))
+    out.append(gg.erdos_renyi(10_000, 20 / 9_999, seed=0))                # the 10k ER workload
+    out.append(gg.planted_partition(n=20_000, q=60, seed=seed, noise=40_000))
+    out.append(gg.rmat(14, 16, seed=seed))
+    out.append(gg.chung_lu(30_000, 24.0, seed=seed))
+    e = gg.from_edges(1000, np.zeros(0, np.int32), np.zeros(0, np.int32))   # edgeless
+    out.append(e)
+    star = gg.from_edges(2000, np.zeros(1999, np.int32), np.arange(1, 2000, dtype=np.int32))
+    out.append(star)
+    k = 60
+    iu, ju = np.triu_indices(k, 1)
+    out.append(gg.from_edges(k, iu.astype(np.int32), ju.astype(np.int32)))   # clique
+    return out
+
+
+def oracle_run(ora, g, order, algo, eps):
+    lab, r, ar, st = ora.rounds(g.off, g.col, order, algo, eps, 1, stats_cap=1_000_000,
+                                want_active_round=True)
+    return lab, r, ar, st
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 5), (768, 1), (769, 2), (10_000, 0), (100_003, 7),
+                                    (1 << 20, 3), ((1 << 20) + 12345, 2**63 + 5)])
+def test_permutation_matches_oracle(cc, ora, gg, n, seed):
+    g = gg.from_edges(n, np.zeros(0, np.int32), np.zeros(0, np.int32))
+    with cc.Graph(g.off, g.col) as graph:
+        assert np.array_equal(graph.permutation(seed), ora.permutation(n, seed))
+
+
+@pytest.mark.parametrize("algo", ["c4", "cw"])
+@pytest.mark.parametrize("eps", [0.1, 0.5, 0.9, 1.0])
+def test_cluster_matches_oracle(cc, ora, gg, algo, eps):
+    a = 1 if algo == "c4" else 2
+    for gi, g in enumerate(small_graphs(gg, 3)):
+        with cc.Graph(g.off, g.col) as graph:
+            for seed in (0, 1, 12345):
+                order = ora.permutation(g.n, seed)
+                olab, orr, ar, ost = oracle_run(ora, g, order, a, eps)
+                lab, r, d, st = graph.cluster(algo, eps, seed, stats_cap=100_000)
+                assert np.array_equal(lab, olab), (gi, seed)
+                assert r == orr
+                for f in STAT_FIELDS:
+                    assert np.array_equal(st[f], ost[f]), (gi, seed, f)
+                assert d == ora.disagreements(g.off, g.col, olab)
+                if a == 1:
+                    assert np.array_equal(lab, ora.kwik(g.off, g.col, order))
+
+
+def test_er10k_many_permutations(cc, ora, gg):
+    """The 10k ER workload over the paper's protocol of many random orders."""
+    g = gg.erdos_renyi(10_000, 20 / 9_999, seed=0)
+    with cc.Graph(g.off, g.col) as graph:
+        for seed in range(40):
+            order = ora.permutation(g.n, seed)
+            lab, _, d = graph.cluster("c4", 0.5, seed)
+            assert np.array_equal(lab, ora.kwik(g.off, g.col, order))
+            olab, orr, _, _ = ora.rounds(g.off, g.col, order, 2, 0.5)
+            lab, r, d = graph.cluster("cw", 0.5, seed)
+            assert np.array_equal(lab, olab) and r == orr
+            assert d == ora.disagreements(g.off, g.col, olab)
+
+
+def test_singleton_batches_equal_kwikcluster(cc, ora, gg):
+    g = gg.rmat(12, 8, seed=4)
+    order = ora.permutation(g.n, 2)
+    kc = ora.kwik(g.off, g.col, order)
+    with cc.Graph(g.off, g.col) as graph:
+        for algo in ("c4", "cw"):
+            lab, r, d = graph.cluster(algo, 1e-6, 2)
+            assert np.array_equal(lab, kc)
+
+
+def test_invariants_and_round_structure_on_gpu_output(cc, ora, gg):
+    g = gg.chung_lu(5000, 16.0, seed=9)
+    with cc.Graph(g.off, g.col) as graph:
+        for algo, a in (("c4", 1), ("cw", 2)):
+            order = ora.permutation(g.n, 77)
+            lab, r, d, st = graph.cluster(algo, 0.5, 77, stats_cap=100_000)
+            chk.check_partition_invariants(g.off, g.col, lab)
+            _, _, ar, _ = ora.rounds(g.off, g.col, order, a, 0.5, 1, want_active_round=True)
+            chk.check_round_structure(g.off, g.col, order, lab, ar, st, 500_000, a, ora.batch_size)
+            chk.check_min_rank_center(g.off, g.col, order, lab, ar, a)
+
+
+def test_disagreements_of_arbitrary_labels(cc, ora, gg):
+    rng = np.random.default_rng(8)
+    g = gg.planted_partition(n=50_000, q=200, seed=2, noise=100_000)
+    with cc.Graph(g.off, g.col) as graph:
+        assert graph.disagreements(g.aux) == ora.disagreements(g.off, g.col, g.aux)
+        for _ in range(3):
+            lab = rng.integers(0, rng.integers(1, g.n), g.n).astype(np.int32)
+            assert graph.disagreements(lab) == ora.disagreements(g.off, g.col, lab)
+        assert graph.disagreements(np.arange(g.n, dtype=np.int32)) == g.m
+        with pytest.raises(cc.CCError):
+            graph.disagreements(np.full(g.n, g.n, np.int32))
+
+
+def test_device_pointers_and_determinism(cc, ora, gg):
+    import torch
+    g = gg.rmat(13, 16, seed=1)
+    off = torch.from_numpy(g.off).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    with cc.Graph(off, col) as graph:
+        out = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for algo in ("c4", "cw"):
+            graph.cluster(algo, 0.5, 3, labels_out=out)
+            torch.cuda.synchronize()
+            first = out.cpu().numpy().copy()
+            lab, _, _ = graph.cluster(algo, 0.5, 3)
+            assert np.array_equal(first, lab)
+            order = ora.permutation(g.n, 3)
+            olab, _, _, _ = ora.rounds(g.off, g.col, order, 1 if algo == "c4" else 2, 0.5)
+            assert np.array_equal(lab, olab)
+
+
+def test_invalid_arguments_and_graphs(cc, gg):
+    g = gg.rmat(8, 4, seed=0)
+    with cc.Graph(g.off, g.col) as graph:
+        for eps in (0.0, -0.5, 1.5, float("nan")):
+            with pytest.raises(cc.CCError) as ei:
+                graph.cluster("cw", eps, 0)
+            assert ei.value.status == -1
+        # the graph stays usable after an invalid argument
+        graph.cluster("cw", 0.5, 0)
+    bad = []
+    off = np.array([0, 1, 1], np.int64)
+    bad.append((off, np.array([1], np.int32)))                 # asymmetric
+    bad.append((np.array([0, 1, 2], np.int64), np.array([0, 0], np.int32)))   # self loops
+    bad.append((np.array([0, 2, 3, 4], np.int64), np.array([2, 1, 0, 0], np.int32)))  # unsorted row
+    bad.append((np.array([0, 1, 2], np.int64), np.array([1, 5], np.int32)))   # out of range
+    bad.append((np.array([0, 2, 1], np.int64), np.array([1, 0], np.int32)))   # decreasing offsets
+    for off, col in bad:
+        with pytest.raises(cc.CCError) as ei:
+            cc.Graph(off, col)
+        assert ei.value.status == -2
+
+
+def test_planted_partition_1m_all_eps(cc, ora, gg):
+    """The planted-partition workload at full size (n = 10^6, 2,000 Zipf
+    clusters, 4M noise edges): C4 = KwikCluster, ClusterWild! = oracle rounds,
+    at eps in {0.1, 0.5, 0.9}; D of the planted labels."""
+    g = gg.workload("planted1m")
+    with cc.Graph(g.off, g.col) as graph:
+        assert graph.disagreements(g.aux) == ora.disagreements(g.off, g.col, g.aux)
+        order = ora.permutation(g.n, 0)
+        kc = ora.kwik(g.off, g.col, order)
+        dkc = ora.disagreements(g.off, g.col, kc)
+        for eps in (0.1, 0.5, 0.9):
+            lab, r, d = graph.cluster("c4", eps, 0)
+            assert np.array_equal(lab, kc) and d == dkc
+            olab, orr, _, _ = ora.rounds(g.off, g.col, order, 2, eps)
+            lab, r, d = graph.cluster("cw", eps, 0)
+            assert np.array_equal(lab, olab) and r == orr
+            assert d == ora.disagreements(g.off, g.col, olab)
