@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark: C4 and ClusterWild! clustering of a ~1B-edge graph on GB300.
+
+Workload: R-MAT scale 26, edge factor 16, (a,b,c,d) = (0.57,0.19,0.19,0.05),
+symmetrised, deduplicated, self loops removed (about 1.07e9 undirected edges,
+2.1e9 CSR entries), seeded synthetic stand-in for the billion-edge web crawls
+of the paper's experiments.  One step = one C4 and one ClusterWild!
+clustering at eps = 0.5, each on a fresh permutation: permutation, all Alg. 2
+rounds, fused objective, labels written to device memory.  The CSR (8.6 GB)
+and the state arrays (0.5 GB) are far larger than L2, so no flush is needed
+between steps.
+
+Metric: undirected edges clustered per second (m * clusterings / time).
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+instead, on a bounded sample of the same generator (R-MAT scale 22).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edges/s clustered (C4 + ClusterWild!, eps=0.5) at 1B edges"
+SAMPLE_SCALE = 22          # CPU sample: same R-MAT generator, 1/16 of the vertices
+KERNELS_PER_CLUSTERING = 8  # 5 permutation kernels + state init + rounds + labels
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="rmat26")
+    p.add_argument("--eps", type=float, default=0.5)
+    p.add_argument("--algos", default="cw,c4")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def step_seeds(rank: int, step: int, n_algos: int, base: int = 1000):
+    """Seeds of one step on one rank: every (rank, step, algo) gets its own pi."""
+    return [base + ((rank * 1_000_003 + step) * n_algos + i) for i in range(n_algos)]
+
+
+def aggregate(edges_per_rank, ms_per_rank):
+    """Whole-job throughput: all ranks' work over the slowest rank's time."""
+    t = max(ms_per_rank)
+    return sum(edges_per_rank) / (t / 1e3), t
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "lines", []):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_graph(workload: str):
+    import graphgen
+    graphgen.build()
+    return graphgen.workload(workload)
+
+
+def measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def rounds_algorithmic_bytes(edges_scanned: int, n: int) -> int:
+    """Bytes the round kernel must move for one clustering: every scanned
+    adjacency entry reads its 4-byte column id and the neighbour's 8-byte state
+    word; every vertex costs its two row offsets (16), its own state read and
+    write (16) and its alive-list entry (4)."""
+    return 12 * edges_scanned + 36 * n
+
+
+def cpu_sample_run(algos, eps, seed_base=7):
+    """One pass of the oracle (permutation + Alg. 2 rounds) per algorithm on
+    the R-MAT scale-22 sample; returns (edges, seconds)."""
+    import graphgen
+    import oracle
+    oracle.build()
+    g = graphgen.rmat(SAMPLE_SCALE, 16, seed=0)
+    t0 = time.perf_counter()
+    for i, a in enumerate(algos):
+        order = oracle.permutation(g.n, seed_base + i)
+        oracle.rounds(g.off, g.col, order, 1 if a == "c4" else 2, eps, 1)
+    dt = time.perf_counter() - t0
+    return g.m * len(algos), dt
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if world > 1 and rank != 0:
+        return
+    algos = args.algos.split(",")
+    for _ in range(args.warmup):
+        cpu_sample_run(algos, args.eps)
+    edges = 0
+    secs = 0.0
+    for s in range(args.steps):
+        e, dt = cpu_sample_run(algos, args.eps, seed_base=100 + s)
+        edges += e
+        secs += dt
+    value = edges / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic",
+        "config": {"workload": f"rmat{SAMPLE_SCALE} (sample of the rmat26 workload's generator)",
+                   "algos": algos, "eps": args.eps},
+        "cpu_baseline": {"value": value, "unit": "edges/s", "cores": 1, "kind": "oracle",
+                         "sample": f"serial C oracle: permutation + Alg. 2 rounds, R-MAT scale {SAMPLE_SCALE}"},
+        "e2e": {"value": value, "unit": "edges/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import paper_1507_05086_gb300 as cc
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    algos = args.algos.split(",")
+    g = load_graph(args.workload)
+    m = g.m
+    graph = cc.Graph(g.off, g.col)
+    graph.set_timing(True)
+    labels = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+
+    for s in range(args.warmup):
+        for a, seed in zip(algos, step_seeds(rank, -1 - s, len(algos))):
+            graph.cluster(a, args.eps, seed, labels_out=labels)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    per = {a: {"ms": [], "rounds_ms": [], "perm_ms": [], "rounds": [], "D": [], "edges": []} for a in algos}
+    with ClockSampler(local_rank) as clocks:
+        barrier()
+        torch.cuda.synchronize()
+        start = torch.cuda.Event(enable_timing=True)
+        end = torch.cuda.Event(enable_timing=True)
+        start.record()
+        for s in range(args.steps):
+            for a, seed in zip(algos, step_seeds(rank, s, len(algos))):
+                _, r, d, st = graph.cluster(a, args.eps, seed, labels_out=labels, stats_cap=100_000)
+                pm, rm, lm = graph.last_timings()
+                per[a]["ms"].append(pm + rm + lm)
+                per[a]["perm_ms"].append(pm)
+                per[a]["rounds_ms"].append(rm)
+                per[a]["rounds"].append(r)
+                per[a]["D"].append(d)
+                per[a]["edges"].append(int(st["edges"].sum()))
+        end.record()
+        torch.cuda.synchronize()
+        barrier()
+    elapsed = start.elapsed_time(end)
+    clusterings = args.steps * len(algos)
+    edges_done = m * clusterings
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed, float(edges_done)], dtype=torch.float64, device="cuda")
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        value, tmax = t[1].item() / (mx[0].item() / 1e3), mx[0].item()
+    else:
+        value, tmax = aggregate([edges_done], [elapsed])
+
+    # roofline of the dominant kernel (the persistent round kernel)
+    peak, peak_kind = measured_hbm_peak()
+    rk_ms = [x for a in algos for x in per[a]["rounds_ms"]]
+    rk_bytes = [rounds_algorithmic_bytes(e, g.n) for a in algos for e in per[a]["edges"]]
+    achieved = (sum(rk_bytes) / 1e9) / (sum(rk_ms) / 1e3)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_rounds", "peak_kind": peak_kind,
+                "bytes_per_launch": sum(rk_bytes) / len(rk_bytes), "ms_per_launch": sum(rk_ms) / len(rk_ms)}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        off_h = torch.from_numpy(g.off).pin_memory()
+        col_h = torch.from_numpy(g.col).pin_memory()
+        lab_h = torch.empty(max(g.n, 1), dtype=torch.int32).pin_memory()
+        torch.cuda.synchronize()
+        es = torch.cuda.Event(enable_timing=True)
+        ee = torch.cuda.Event(enable_timing=True)
+        es.record()
+        for s in range(args.e2e_steps):
+            with cc.Graph(off_h.numpy(), col_h.numpy()) as gh:
+                for a, seed in zip(algos, step_seeds(rank, 10_000 + s, len(algos))):
+                    gh.cluster(a, args.eps, seed, labels_out=lab_h.numpy())
+        ee.record()
+        torch.cuda.synchronize()
+        e_ms = es.elapsed_time(ee)
+        e2e = {"value": m * len(algos) * args.e2e_steps / (e_ms / 1e3), "unit": "edges/s",
+               "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz,
+               "d2h_bytes_per_step": (4 * g.n + 16) * len(algos),
+               "ms_per_step": e_ms / args.e2e_steps,
+               "what": "per step: cc_graph_create from pinned host CSR (copy + validation), one C4 and one "
+                       "ClusterWild! cc_cluster with labels to pinned host memory, cc_graph_destroy"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        e, dt = cpu_sample_run(algos, args.eps)
+        cpu = {"value": e / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
+               "sample": f"serial C oracle (permutation + Alg. 2 rounds, C4 and ClusterWild!, eps={args.eps}) "
+                         f"on R-MAT scale {SAMPLE_SCALE} from the same generator, {e // len(algos)} edges, "
+                         f"{dt:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "edges/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": tmax / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: R-MAT scale 26, ef 16, (0.57,0.19,0.19,0.05), seed 0"
+                       if args.workload == "rmat26" else args.workload,
+                       "n": g.n, "m": m, "nnz": g.nnz, "max_degree": graph.max_degree, "algos": algos,
+                       "eps": args.eps, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (CSR and state far above 129 MB); no flush"},
+            "per_algo": {a: {"ms_per_clustering": statistics.mean(per[a]["ms"]),
+                             "rounds_kernel_ms": statistics.mean(per[a]["rounds_ms"]),
+                             "permutation_ms": statistics.mean(per[a]["perm_ms"]),
+                             "rounds": per[a]["rounds"][0], "disagreements": per[a]["D"],
+                             "edges_scanned": per[a]["edges"][0],
+                             "edges_per_s": m / (statistics.mean(per[a]["ms"]) / 1e3)} for a in algos},
+            "clocks": clocks.summary(),
+            "e2e": e2e,
+            "gpu_launches": KERNELS_PER_CLUSTERING * clusterings,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    graph.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

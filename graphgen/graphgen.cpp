@@ -112,14 +112,45 @@ void build_csr(int64_t n, const int32_t* u, const int32_t* v, int64_t m, int thr
   off[0] = 0;
   for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + cnt[i].load(std::memory_order_relaxed);
   std::vector<int32_t> col(off[n] > 0 ? off[n] : 1);
+  // Rows above kHub entries are split into one contiguous sub-range per
+  // thread (no shared cache lines while filling); other rows use an atomic
+  // cursor.
+  constexpr uint32_t kHub = 1024;
+  std::vector<int32_t> hub_of(n > 0 ? n : 1, -1);
+  std::vector<int64_t> hubs;
+  for (int64_t i = 0; i < n; ++i)
+    if (cnt[i].load(std::memory_order_relaxed) > kHub) { hub_of[i] = (int32_t)hubs.size(); hubs.push_back(i); }
+  const int64_t H = (int64_t)hubs.size();
+  const int T = (int)std::max<int64_t>(1, std::min<int64_t>(threads, m > 0 ? m : 1));
+  std::vector<int64_t> hub_cur((size_t)T * (H > 0 ? H : 1), 0);
+  parallel_for(m, T, [&](int64_t b, int64_t e, int t) {
+    int64_t* hc = hub_cur.data() + (size_t)t * H;
+    for (int64_t i = b; i < e; ++i) {
+      if (u[i] < 0 || u[i] == v[i]) continue;
+      if (hub_of[u[i]] >= 0) ++hc[hub_of[u[i]]];
+      if (hub_of[v[i]] >= 0) ++hc[hub_of[v[i]]];
+    }
+  });
+  for (int64_t h = 0; h < H; ++h) {          // per-thread start inside each hub row
+    int64_t run = off[hubs[h]];
+    for (int t = 0; t < T; ++t) {
+      int64_t c = hub_cur[(size_t)t * H + h];
+      hub_cur[(size_t)t * H + h] = run;
+      run += c;
+    }
+  }
   parallel_for(n, threads, [&](int64_t b, int64_t e, int) {
     for (int64_t i = b; i < e; ++i) cnt[i].store(0, std::memory_order_relaxed);
   });
-  parallel_for(m, threads, [&](int64_t b, int64_t e, int) {
+  parallel_for(m, T, [&](int64_t b, int64_t e, int t) {
+    int64_t* hc = hub_cur.data() + (size_t)t * H;
     for (int64_t i = b; i < e; ++i) {
       if (u[i] < 0 || u[i] == v[i]) continue;
-      col[off[u[i]] + cnt[u[i]].fetch_add(1, std::memory_order_relaxed)] = v[i];
-      col[off[v[i]] + cnt[v[i]].fetch_add(1, std::memory_order_relaxed)] = u[i];
+      const int32_t a = u[i], c = v[i];
+      if (hub_of[a] >= 0) col[hc[hub_of[a]]++] = c;
+      else col[off[a] + cnt[a].fetch_add(1, std::memory_order_relaxed)] = c;
+      if (hub_of[c] >= 0) col[hc[hub_of[c]]++] = a;
+      else col[off[c] + cnt[c].fetch_add(1, std::memory_order_relaxed)] = a;
     }
   });
   // sort + dedup each row; new lengths into cnt
@@ -140,9 +171,7 @@ void build_csr(int64_t n, const int32_t* u, const int32_t* v, int64_t m, int thr
     if (len && g->off[i] != off[i])
       std::memmove(col.data() + g->off[i], col.data() + off[i], (size_t)len * sizeof(int32_t));
   }
-  col.resize(g->off[n] > 0 ? g->off[n] : 1);
-  col.shrink_to_fit();
-  g->col.swap(col);
+  g->col.swap(col);   // capacity may exceed off[n]; only the prefix is used
 }
 
 }  // namespace
@@ -273,15 +302,11 @@ int gg_rmat(int scale, int64_t ef, double a, double b, double c, uint64_t seed, 
       for (int l = 0; l < scale; ++l) {
         uint64_t r;
         if ((l & 1) == 0) { word = rng.next(); r = word >> 32; } else { r = word & 0xFFFFFFFFull; }
-        uint32_t bit = 1u << (scale - 1 - l);
-        if (r < ta) {
-        } else if (r < tb) {
-          colv |= bit;
-        } else if (r < tc) {
-          row |= bit;
-        } else {
-          row |= bit; colv |= bit;
-        }
+        // quadrant a: (0,0), b: (0,1), c: (1,0), d: (1,1)
+        const uint32_t rbit = r >= tb ? 1u : 0u;
+        const uint32_t cbit = ((r >= ta) & (r < tb)) | (r >= tc) ? 1u : 0u;
+        row = (row << 1) | rbit;
+        colv = (colv << 1) | cbit;
       }
       us[i] = (int32_t)row;
       vs[i] = (int32_t)colv;
@@ -338,6 +363,7 @@ int gg_from_edges(int64_t n, const int32_t* u, const int32_t* v, int64_t m, int 
 
 int64_t gg_n(const gg_graph* g) { return g->n; }
 int64_t gg_nnz(const gg_graph* g) { return g->off.empty() ? 0 : g->off[g->n]; }
+
 int64_t gg_aux_len(const gg_graph* g) { return (int64_t)g->aux.size(); }
 
 int gg_copy(const gg_graph* g, int64_t* off, int32_t* col, int32_t* aux) {

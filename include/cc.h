@@ -160,6 +160,17 @@ int cc_batch_run(cc_graph* const* gs, int32_t count, int algo, double eps,
                  const uint64_t* seeds, int32_t k_perms, int32_t* const* labels_out,
                  int32_t* best_j, int64_t* best_D, int32_t* rounds);
 
+/*
+ * Kernel timing hook.  cc_graph_set_timing(g, 1) makes later cc_cluster /
+ * cc_cluster_ex calls on g record CUDA events on the graph's stream around
+ * their three device stages; cc_last_timings then writes the durations in
+ * milliseconds of the last call to ms_out[0..2] = {permutation, rounds
+ * kernel, label output}.  cc_last_timings returns CC_ERR_INVALID_ARG when
+ * timing is off or nothing has been timed yet.
+ */
+int cc_graph_set_timing(cc_graph* g, int enable);
+int cc_last_timings(const cc_graph* g, float* ms_out);
+
 /* Human-readable name of a status code (static storage). */
 const char* cc_status_string(int status);
 

@@ -37,6 +37,11 @@ struct cc_graph {
   RoundStat* stats_dev = nullptr;
   int64_t stats_dev_cap = 0;
   int* perm_err = nullptr;
+  // optional event timing of the last clustering
+  bool timing = false;
+  bool timed = false;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  float last_ms[3] = {0, 0, 0};
   // pinned host staging for the small results
   Ctl* ctl_host = nullptr;
   unsigned long long* obj_host = nullptr;
@@ -154,6 +159,8 @@ int cc_graph_destroy(cc_graph* g) {
   dfree(g->stats_dev, s);
   dfree(g->perm_err, s);
   cudaStreamSynchronize(s);
+  for (auto& e : g->ev)
+    if (e) cudaEventDestroy(e);
   if (g->ctl_host) cudaFreeHost(g->ctl_host);
   if (g->obj_host) cudaFreeHost(g->obj_host);
   delete g;
@@ -305,8 +312,11 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
   b.stats = g->stats_dev;
   b.stats_cap = stats_cap;
   CC_TRY(cudaMemsetAsync(g->perm_err, 0, sizeof(int), s));
+  if (g->timing) CC_TRY(cudaEventRecord(g->ev[0], s));
   CC_TRY(launch_permutation(g->n, seed, g->order, g->perm_ws, g->num_sms, g->perm_err, s));
+  if (g->timing) CC_TRY(cudaEventRecord(g->ev[1], s));
   CC_TRY(launch_rounds(b, algo, ppm, g->grid, s));
+  if (g->timing) CC_TRY(cudaEventRecord(g->ev[2], s));
   const bool dev = is_device_ptr(labels_out);
   if (labels_out) {
     if (dev) {
@@ -317,11 +327,16 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
       CC_TRY(cudaMemcpyAsync(labels_out, g->labels_tmp, 4 * (size_t)g->n, cudaMemcpyDeviceToHost, s));
     }
   }
+  if (g->timing) CC_TRY(cudaEventRecord(g->ev[3], s));
   CC_TRY(cudaMemcpyAsync(g->ctl_host, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
   int perr = 0;
   CC_TRY(cudaMemcpyAsync(&perr, g->perm_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   CC_TRY(cudaStreamSynchronize(s));
   const Ctl& c = *g->ctl_host;
+  if (g->timing) {
+    for (int i = 0; i < 3; ++i) CC_TRY(cudaEventElapsedTime(&g->last_ms[i], g->ev[i], g->ev[i + 1]));
+    g->timed = true;
+  }
   if (perr != 0) return status_of_device_err(perr);
   if (c.err != 0) return status_of_device_err(c.err);
   if (c.n_alive != 0 || !c.done) return CC_ERR_INTERNAL;
@@ -337,6 +352,23 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
     const int64_t m = g->nnz / 2;
     *disagreements_out = m - 2 * (int64_t)c.mc - (int64_t)c.mm + (int64_t)c.pairs;
   }
+  return CC_OK;
+}
+
+int cc_graph_set_timing(cc_graph* g, int enable) {
+  if (!g) return CC_ERR_INVALID_ARG;
+  cudaSetDevice(g->device);
+  if (enable)
+    for (auto& e : g->ev)
+      if (!e) CC_TRY(cudaEventCreate(&e));
+  g->timing = enable != 0;
+  g->timed = false;
+  return CC_OK;
+}
+
+int cc_last_timings(const cc_graph* g, float* ms_out) {
+  if (!g || !ms_out || !g->timing || !g->timed) return CC_ERR_INVALID_ARG;
+  for (int i = 0; i < 3; ++i) ms_out[i] = g->last_ms[i];
   return CC_OK;
 }
 

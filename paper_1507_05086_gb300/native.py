@@ -78,6 +78,10 @@ def load(build_if_missing: bool = True):
         lib.cc_cluster_ex.argtypes = [vp, ci, ctypes.c_double, u64, vp, vp, vp, vp, i32, vp]
         lib.cc_disagreements.restype = ci
         lib.cc_disagreements.argtypes = [vp, vp, vp]
+        lib.cc_graph_set_timing.restype = ci
+        lib.cc_graph_set_timing.argtypes = [vp, ci]
+        lib.cc_last_timings.restype = ci
+        lib.cc_last_timings.argtypes = [vp, vp]
         lib.cc_batch_run.restype = ci
         lib.cc_batch_run.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp, vp, vp]
         _lib = lib
@@ -190,6 +194,15 @@ class Graph:
         _check("cc_cluster", self._lib.cc_cluster(self._h, a, float(eps), seed & (2**64 - 1), _ptr(labels_out),
                                                   ctypes.byref(rounds), ctypes.byref(d)))
         return labels_out, rounds.value, d.value
+
+    def set_timing(self, enable: bool = True):
+        _check("cc_graph_set_timing", self._lib.cc_graph_set_timing(self._h, 1 if enable else 0))
+
+    def last_timings(self):
+        """(permutation, rounds kernel, labels) milliseconds of the last clustering."""
+        ms = (ctypes.c_float * 3)()
+        _check("cc_last_timings", self._lib.cc_last_timings(self._h, ctypes.cast(ms, ctypes.c_void_p)))
+        return tuple(float(x) for x in ms)
 
     def disagreements(self, labels) -> int:
         if isinstance(labels, np.ndarray):
