@@ -206,7 +206,8 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
-    per = {a: {"ms": [], "rounds_ms": [], "perm_ms": [], "rounds": [], "D": [], "edges": []} for a in algos}
+    per = {a: {"ms": [], "rounds_ms": [], "perm_ms": [], "rounds": [], "D": [], "edges": [], "phases": []}
+           for a in algos}
     with ClockSampler(local_rank) as clocks:
         barrier()
         torch.cuda.synchronize()
@@ -223,6 +224,7 @@ def run_ours(args):
                 per[a]["rounds"].append(r)
                 per[a]["D"].append(d)
                 per[a]["edges"].append(int(st["edges"].sum()))
+                per[a]["phases"].append(graph.last_phase_times())
         end.record()
         torch.cuda.synchronize()
         barrier()
@@ -295,6 +297,8 @@ def run_ours(args):
                              "permutation_ms": statistics.mean(per[a]["perm_ms"]),
                              "rounds": per[a]["rounds"][0], "disagreements": per[a]["D"],
                              "edges_scanned": per[a]["edges"][0],
+                             "phase_ms": {k: statistics.mean(p[k] for p in per[a]["phases"])
+                                          for k in per[a]["phases"][0]},
                              "edges_per_s": m / (statistics.mean(per[a]["ms"]) / 1e3)} for a in algos},
             "clocks": clocks.summary(),
             "e2e": e2e,

@@ -171,6 +171,15 @@ int cc_batch_run(cc_graph* const* gs, int32_t count, int algo, double eps,
 int cc_graph_set_timing(cc_graph* g, int enable);
 int cc_last_timings(const cc_graph* g, float* ms_out);
 
+/*
+ * Device-side breakdown of the last clustering's round kernel (always
+ * recorded; globaltimer at every grid barrier).  ms_out[0..min(cap,7)) =
+ * milliseconds spent in: alive-list rebuild (count), rebuild (compact and
+ * refill), active-set count, active-set emit, centers + attachment, C4
+ * fixpoint and blocked actives, removal and degree updates.
+ */
+int cc_last_phase_times(const cc_graph* g, double* ms_out, int32_t cap);
+
 /* Human-readable name of a status code (static storage). */
 const char* cc_status_string(int status);
 

@@ -42,6 +42,8 @@ struct cc_graph {
   bool timed = false;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   float last_ms[3] = {0, 0, 0};
+  unsigned long long last_phase_ns[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  bool phases_valid = false;
   // pinned host staging for the small results
   Ctl* ctl_host = nullptr;
   unsigned long long* obj_host = nullptr;
@@ -223,27 +225,32 @@ int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, 
       g->own_col = true;
       if (nnz > 0 && (rc = from_cuda(cudaMemcpyAsync(g->col, col_idx, 4 * (size_t)nnz, cudaMemcpyHostToDevice, s))) != CC_OK) break;
     }
-    // validation
+    // validation: offsets first (the non-empty-row list relies on them)
     void* vws = nullptr;
     if ((rc = from_cuda(dalloc(&vws, validate_workspace_bytes(), s))) != CC_OK) break;
-    launch_validate(n, nnz, g->off, g->col, vws, g->num_sms, s);
+    int* vflags_dev = reinterpret_cast<int*>(static_cast<char*>(vws) + align_up(8 * sizeof(unsigned long long)));
     int vflags[2] = {0, 0};
-    cudaMemcpyAsync(vflags, static_cast<char*>(vws) + align_up(8 * sizeof(unsigned long long)), sizeof(vflags),
-                    cudaMemcpyDeviceToHost, s);
-    // non-empty rows (for the edge-balanced objective pass)
-    if ((rc = from_cuda(dalloc(&g->nz_row, 4 * (size_t)(n > 0 ? n : 1), s))) != CC_OK) break;
-    if ((rc = from_cuda(dalloc(&g->nz_pos, 8 * (size_t)(n > 0 ? n : 1), s))) != CC_OK) break;
+    launch_validate_offsets(n, nnz, g->off, vws, g->num_sms, s);
+    cudaMemcpyAsync(vflags, vflags_dev, sizeof(vflags), cudaMemcpyDeviceToHost, s);
+    if ((rc = from_cuda(cudaStreamSynchronize(s))) != CC_OK) { dfree(vws, s); break; }
+    if (vflags[0] != 0) { dfree(vws, s); rc = CC_ERR_INVALID_GRAPH; break; }
+    g->max_deg = vflags[1];
+    // non-empty rows (for the edge-balanced passes over the whole CSR)
+    if ((rc = from_cuda(dalloc(&g->nz_row, 4 * (size_t)(n > 0 ? n : 1), s))) != CC_OK) { dfree(vws, s); break; }
+    if ((rc = from_cuda(dalloc(&g->nz_pos, 8 * (size_t)(n > 0 ? n : 1), s))) != CC_OK) { dfree(vws, s); break; }
     void* nws = nullptr;
-    if ((rc = from_cuda(dalloc(&nws, nonempty_workspace_bytes(n), s))) != CC_OK) break;
+    if ((rc = from_cuda(dalloc(&nws, nonempty_workspace_bytes(n), s))) != CC_OK) { dfree(vws, s); break; }
     int64_t* nz_dev = reinterpret_cast<int64_t*>(static_cast<char*>(nws) + nonempty_workspace_bytes(n) - 256);
     launch_nonempty_rows(n, g->off, g->nz_row, g->nz_pos, nws, nz_dev, g->num_sms, s);
     cudaMemcpyAsync(&g->nz_n, nz_dev, 8, cudaMemcpyDeviceToHost, s);
+    if ((rc = from_cuda(cudaStreamSynchronize(s))) != CC_OK) { dfree(vws, s); dfree(nws, s); break; }
+    launch_validate_edges(n, nnz, g->nz_row, g->nz_pos, g->nz_n, g->col, vws, g->num_sms, s);
+    cudaMemcpyAsync(vflags, vflags_dev, sizeof(vflags), cudaMemcpyDeviceToHost, s);
     dfree(vws, s);
     dfree(nws, s);
     if ((rc = from_cuda(cudaStreamSynchronize(s))) != CC_OK) break;
     if ((rc = from_cuda(cudaGetLastError())) != CC_OK) break;
     if (vflags[0] != 0) { rc = CC_ERR_INVALID_GRAPH; break; }
-    g->max_deg = vflags[1];
   } while (false);
   if (rc != CC_OK) {
     cc_graph_destroy(g);
@@ -337,6 +344,8 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
     for (int i = 0; i < 3; ++i) CC_TRY(cudaEventElapsedTime(&g->last_ms[i], g->ev[i], g->ev[i + 1]));
     g->timed = true;
   }
+  for (int i = 0; i < 8; ++i) g->last_phase_ns[i] = c.ph_ns[i];
+  g->phases_valid = true;
   if (perr != 0) return status_of_device_err(perr);
   if (c.err != 0) return status_of_device_err(c.err);
   if (c.n_alive != 0 || !c.done) return CC_ERR_INTERNAL;
@@ -369,6 +378,12 @@ int cc_graph_set_timing(cc_graph* g, int enable) {
 int cc_last_timings(const cc_graph* g, float* ms_out) {
   if (!g || !ms_out || !g->timing || !g->timed) return CC_ERR_INVALID_ARG;
   for (int i = 0; i < 3; ++i) ms_out[i] = g->last_ms[i];
+  return CC_OK;
+}
+
+int cc_last_phase_times(const cc_graph* g, double* ms_out, int32_t cap) {
+  if (!g || !ms_out || cap < 0 || !g->phases_valid) return CC_ERR_INVALID_ARG;
+  for (int32_t i = 0; i < cap && i < 7; ++i) ms_out[i] = (double)g->last_phase_ns[i] * 1e-6;
   return CC_OK;
 }
 

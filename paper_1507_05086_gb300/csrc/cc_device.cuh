@@ -195,81 +195,233 @@ __device__ __forceinline__ T block_max(T x, T* scratch) {
 //
 // Item j of the list owns the virtual edges [epos[j], epos[j+1]) (epos[j] is
 // non-decreasing in j and every item owns at least one edge); E is the total.
-// Every warp of the grid takes chunks of kLbsChunk consecutive virtual edges,
-// so a hub row is spread over many warps and short rows are packed together.
-// f(valid, j, k) is called by all 32 lanes of a warp together for each step of
-// 32 edges, with k the edge's index inside item j's row; lanes with
-// valid == false must do nothing but take part in warp collectives.
+// Warps take chunks of kLbsBatches * kLbsW consecutive virtual edges, so a hub
+// row is spread over many warps and short rows are packed together.  Within a
+// chunk a warp handles kLbsW = 32 * kLbsK edges at a time: each lane gets kLbsK
+// edges (e = base + lane + 32 t), so kLbsK independent loads per lane are in
+// flight instead of one.  f(L) receives an Lbs view of the batch (item, virtual
+// edge and position in the item of each of the lane's edges); all 32 lanes
+// call f together (edges with L.ok(t) == false must be skipped, but their
+// lanes still take part in warp collectives).
 // ---------------------------------------------------------------------------
-constexpr int kLbsSteps = 8;
-constexpr int64_t kLbsChunk = 32 * kLbsSteps;
+constexpr int kLbsK = 4;
+constexpr int kLbsW = 32 * kLbsK;
+constexpr int kLbsBatches = 4;
 
-__device__ __forceinline__ int64_t upper_bound_i64(const int64_t* a, int64_t n, int64_t x) {
-  int64_t lo = 0, hi = n;
-  while (lo < hi) {
-    int64_t mid = (lo + hi) >> 1;
-    if (ldcg(a + mid) <= x) lo = mid + 1; else hi = mid;
+struct LbsWarp {
+  int32_t mark[kLbsW];   // relative item index per position
+  int32_t rel[kLbsW];    // item start relative to the batch base
+};
+
+// One batch of kLbsW virtual edges as seen by one lane.
+struct Lbs {
+  int64_t j0, base;
+  const LbsWarp* ws;
+  int32_t ri[kLbsK];
+  unsigned valid;
+  __device__ __forceinline__ bool ok(int t) const { return (valid >> t) & 1u; }
+  __device__ __forceinline__ int64_t item(int t) const { return j0 + ri[t]; }
+  __device__ __forceinline__ int64_t edge(int t) const { return base + (threadIdx.x & 31) + 32 * t; }
+  // index of the edge inside its item's row
+  __device__ __forceinline__ int64_t in_row(int t) const {
+    return (int64_t)((threadIdx.x & 31) + 32 * t) - ws->rel[ri[t]];
   }
-  return lo;
+};
+
+// Number of elements of the sorted array a[0..n) that are <= x, by a 33-ary
+// search of the whole warp (about log_33(n) dependent loads).
+__device__ __forceinline__ int64_t warp_upper_bound(const int64_t* a, int64_t n, int64_t x) {
+  const int lane = threadIdx.x & 31;
+  int64_t lo = 0, hi = n;
+  while (hi - lo > 32) {
+    const int64_t span = hi - lo;
+    const int64_t p = lo + (span * (lane + 1)) / 33;
+    const unsigned b = __ballot_sync(FULL, ldcg(a + p) <= x);
+    const int c = __popc(b);
+    const int64_t pp = __shfl_sync(FULL, p, c > 0 ? c - 1 : 0);
+    const int64_t pn = __shfl_sync(FULL, p, c < 32 ? c : 31);
+    lo = c > 0 ? pp + 1 : lo;
+    hi = c < 32 ? pn : hi;
+  }
+  const int64_t p = lo + lane;
+  const bool le = p < hi && ldcg(a + p) <= x;
+  return lo + __popc(__ballot_sync(FULL, le));
 }
 
 template <class F>
-__device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems, int64_t E,
-                                             int* warp_buf /* 32 ints for this warp */, F&& f) {
+__device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems, int64_t E, LbsWarp* ws,
+                                             F&& f) {
   if (E <= 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t base0 = gwarp * kLbsChunk; base0 < E; base0 += nwarps * kLbsChunk) {
-    int64_t j0 = 0;
-    if (lane == 0) j0 = upper_bound_i64(epos, nitems, base0) - 1;
-    j0 = __shfl_sync(FULL, j0, 0);
-    const int64_t end = base0 + kLbsChunk < E ? base0 + kLbsChunk : E;
-    for (int64_t base = base0; base < end; base += 32) {
-      const int64_t jj = j0 + lane;
-      const int64_t s = jj < nitems ? ldcg(epos + jj) : INT64_MAX;
-      warp_buf[lane] = -1;
+  constexpr int64_t kChunk = (int64_t)kLbsW * kLbsBatches;
+  for (int64_t c0 = gwarp * kChunk; c0 < E; c0 += nwarps * kChunk) {
+    int64_t j0 = warp_upper_bound(epos, nitems, c0) - 1;
+    const int64_t cend = c0 + kChunk < E ? c0 + kChunk : E;
+    for (int64_t base = c0; base < cend; base += kLbsW) {
+      int64_t s[kLbsK];
+#pragma unroll
+      for (int t = 0; t < kLbsK; ++t) {
+        const int64_t jj = j0 + lane + 32 * t;
+        s[t] = jj < nitems ? ldcg(epos + jj) : INT64_MAX;
+        ws->mark[lane + 32 * t] = -1;
+      }
       __syncwarp();
-      if (s >= base && s < base + 32) warp_buf[s - base] = lane;
+#pragma unroll
+      for (int t = 0; t < kLbsK; ++t) {
+        const int i = lane + 32 * t;
+        if (s[t] < base + kLbsW) {
+          ws->rel[i] = (int32_t)(s[t] - base);
+          if (s[t] >= base) ws->mark[s[t] - base] = i;
+        }
+      }
       __syncwarp();
-      int t = warp_buf[lane];
+      // segmented max-scan: each position takes the last item starting at or before it
+      int v[kLbsK];
+      int run = -1;
+#pragma unroll
+      for (int t = 0; t < kLbsK; ++t) {
+        const int m = ws->mark[lane * kLbsK + t];
+        run = m > run ? m : run;
+        v[t] = run;
+      }
+      int inc = run;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        int y = __shfl_up_sync(FULL, t, o);
-        if (lane >= o) t = y > t ? y : t;
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc = y > inc ? y : inc;
       }
-      if (t < 0) t = 0;
-      const int64_t sj = __shfl_sync(FULL, s, t);
-      const int64_t e = base + lane;
-      f(e < end, j0 + t, e - sj);
-      j0 += __shfl_sync(FULL, t, 31);
+      int exc = __shfl_up_sync(FULL, inc, 1);
+      if (lane == 0) exc = -1;
       __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kLbsK; ++t) {
+        int m = v[t] > exc ? v[t] : exc;
+        ws->mark[lane * kLbsK + t] = m < 0 ? 0 : m;
+      }
+      __syncwarp();
+      Lbs L;
+      L.j0 = j0;
+      L.base = base;
+      L.ws = ws;
+      L.valid = 0;
+#pragma unroll
+      for (int t = 0; t < kLbsK; ++t) {
+        const int p = lane + 32 * t;
+        L.ri[t] = ws->mark[p];
+        if (base + p < cend) L.valid |= 1u << t;
+      }
+      const int last = ws->mark[kLbsW - 1];
+      f(L);
+      __syncwarp();
+      j0 += last;
     }
   }
 }
 
-// Warp-aggregated append to a list whose counter packs (items << 33 | edges).
-// Lanes with want == true add one item of `edges` edges; the function returns
-// (item index, first edge) for those lanes.  All 32 lanes must call it.
+// Lists of adjacency rows.  A list counter packs (items << 33 | edges): one
+// atomicAdd hands out an item index and the item's first virtual edge, so
+// epos stays non-decreasing in the item index.  For every item the list keeps
+// its vertex, epos and delta = (CSR row start) - epos, so the CSR position of
+// virtual edge e of item j is e + delta[j].
 constexpr int kPackShift = 33;
 constexpr uint64_t kPackEdgeMask = (1ull << kPackShift) - 1;
 
-__device__ __forceinline__ void warp_append_packed(bool want, int64_t edges, unsigned long long* counter,
-                                                   int64_t* item_out, int64_t* epos_out) {
+struct RowList {
+  int32_t* v;
+  int64_t* epos;
+  int64_t* delta;
+  int32_t* aux;                 // optional per-item payload (may be null)
+  unsigned long long* counter;  // packed (items << 33 | edges)
+};
+
+// Warp-aggregated append of one item per lane with want == true.  All 32
+// lanes must call it.
+__device__ __forceinline__ void warp_append_rows(bool want, int32_t v, int64_t row, int64_t edges, int32_t aux,
+                                                 const RowList& L) {
   const int lane = threadIdx.x & 31;
   const unsigned mask = __ballot_sync(FULL, want);
   if (mask == 0) return;
-  const int64_t ex = warp_inclusive_sum<int64_t>(want ? edges : 0) - (want ? edges : 0);
-  const int64_t tot = __shfl_sync(FULL, ex + (want ? edges : 0), 31);
+  const int64_t mine = want ? edges : 0;
+  const int64_t ex = warp_inclusive_sum<int64_t>(mine) - mine;
+  const int64_t tot = __shfl_sync(FULL, ex + mine, 31);
   const int leader = __ffs(mask) - 1;
   unsigned long long old = 0;
   if (lane == leader)
-    old = atomicAdd(counter, ((unsigned long long)__popc(mask) << kPackShift) | (unsigned long long)tot);
+    old = atomicAdd(L.counter, ((unsigned long long)__popc(mask) << kPackShift) | (unsigned long long)tot);
   old = __shfl_sync(FULL, old, leader);
   if (want) {
-    *item_out = (int64_t)(old >> kPackShift) + __popc(mask & ((1u << lane) - 1u));
-    *epos_out = (int64_t)(old & kPackEdgeMask) + ex;
+    const int64_t j = (int64_t)(old >> kPackShift) + __popc(mask & ((1u << lane) - 1u));
+    const int64_t ep = (int64_t)(old & kPackEdgeMask) + ex;
+    L.v[j] = v;
+    L.epos[j] = ep;
+    L.delta[j] = row - ep;
+    if (L.aux) L.aux[j] = aux;
   }
+}
+
+// Per-warp staging of list appends, so that many items share one atomic on
+// the list counter.
+constexpr int kAppCap = 128;
+
+struct AppendBuf {
+  int32_t v[kAppCap];
+  int32_t len[kAppCap];
+  int64_t row[kAppCap];
+  int n;
+};
+
+__device__ __forceinline__ void append_flush(AppendBuf* b, const RowList& L) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  const int n = b->n;
+  if (n == 0) return;
+  constexpr int kPer = kAppCap / 32;
+  int64_t loc = 0;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int i = lane * kPer + q;
+    if (i < n) loc += b->len[i];
+  }
+  const int64_t ex = warp_inclusive_sum<int64_t>(loc) - loc;
+  const int64_t tot = __shfl_sync(FULL, ex + loc, 31);
+  unsigned long long old = 0;
+  if (lane == 0) old = atomicAdd(L.counter, ((unsigned long long)n << kPackShift) | (unsigned long long)tot);
+  old = __shfl_sync(FULL, old, 0);
+  const int64_t j0 = (int64_t)(old >> kPackShift);
+  int64_t ep = (int64_t)(old & kPackEdgeMask) + ex;
+#pragma unroll
+  for (int q = 0; q < kPer; ++q) {
+    const int i = lane * kPer + q;
+    if (i < n) {
+      L.v[j0 + i] = b->v[i];
+      L.epos[j0 + i] = ep;
+      L.delta[j0 + i] = b->row[i] - ep;
+      ep += b->len[i];
+    }
+  }
+  __syncwarp();
+  if (lane == 0) b->n = 0;
+  __syncwarp();
+}
+
+__device__ __forceinline__ void append_stage(AppendBuf* b, bool want, int32_t v, int64_t row, int32_t len,
+                                             const RowList& L) {
+  const int lane = threadIdx.x & 31;
+  const unsigned mask = __ballot_sync(FULL, want);
+  if (mask == 0) return;
+  __syncwarp();
+  if (b->n + __popc(mask) > kAppCap) append_flush(b, L);
+  const int pos = b->n + __popc(mask & ((1u << lane) - 1u));
+  if (want) {
+    b->v[pos] = v;
+    b->len[pos] = len;
+    b->row[pos] = row;
+  }
+  __syncwarp();
+  if (lane == 0) b->n += __popc(mask);
+  __syncwarp();
 }
 
 }  // namespace ccg

@@ -53,6 +53,11 @@ struct Ctl {
   // per-round tallies
   long long r_centers, r_attached, r_noncenter, r_blocked;
   long long r_edges;
+  // time per phase category (ns, booked by barrier leaders): rebuild-count,
+  // rebuild-compact, select-count, select-emit, centers+attach, C4 fixpoint
+  // and blocked actives, removal+decrement
+  unsigned long long ph_ns[8];
+  unsigned long long ph_t0;
   // objective tallies: member-center edges, member-member edges (counted from
   // both ends), sum over clusters of C(size, 2)
   unsigned long long mc, mm, pairs;
@@ -67,13 +72,16 @@ struct RoundBuffers {
   unsigned long long* st;      // per-vertex state word
   int32_t* al0;
   int32_t* al1;
+  // row lists (see RowList in cc_device.cuh): vertex, first virtual edge,
+  // CSR delta; actives also keep their rank, the blocked list stores the
+  // active-list index in place of a vertex
   int32_t* act_v;
   int32_t* act_r;
   int64_t* act_e;
-  int64_t* act_row;
+  int64_t* act_d;
   int32_t* new_v;
   int64_t* new_e;
-  int64_t* new_row;
+  int64_t* new_d;
   int32_t* size;
   int32_t* cnt;                // degree-count table, max_deg + 2 + histogram window
   uint8_t* blk_flag;
@@ -82,6 +90,7 @@ struct RoundBuffers {
   int32_t* pull;
   int32_t* b_j;
   int64_t* b_e;
+  int64_t* b_d;
   int64_t* blk_a;              // per-block scratch
   int64_t* blk_b;
   RoundStat* stats;
@@ -107,10 +116,13 @@ cudaError_t launch_disagreements(int64_t n, int64_t nnz, const int64_t* off, con
                                  const int32_t* labels, void* ws, unsigned long long* out, int num_sms,
                                  cudaStream_t stream);
 size_t validate_workspace_bytes();
-// ws: validate_workspace_bytes(); after completion the int pair at
-// ws + align_up(64) holds (error code, max degree).
-cudaError_t launch_validate(int64_t n, int64_t nnz, const int64_t* off, const int32_t* col, void* ws,
-                            int num_sms, cudaStream_t stream);
+// Validation in two steps sharing ws (validate_workspace_bytes()): offsets
+// first (zeroes ws), then the entries over the non-empty rows.  The int pair
+// at ws + align_up(64) holds (first error code, max degree).
+cudaError_t launch_validate_offsets(int64_t n, int64_t nnz, const int64_t* off, void* ws, int num_sms,
+                                    cudaStream_t stream);
+cudaError_t launch_validate_edges(int64_t n, int64_t nnz, const int32_t* nz_row, const int64_t* nz_pos,
+                                  int64_t nz_n, const int32_t* col, void* ws, int num_sms, cudaStream_t stream);
 cudaError_t launch_offsets_i32_to_i64(int64_t n, const int32_t* in, int64_t* out, cudaStream_t stream);
 size_t nonempty_workspace_bytes(int64_t n);
 cudaError_t launch_nonempty_rows(int64_t n, const int64_t* off, int32_t* nz_row, int64_t* nz_pos, void* ws,

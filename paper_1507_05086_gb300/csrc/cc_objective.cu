@@ -30,15 +30,20 @@ __global__ void __launch_bounds__(kObjThreads) k_intra(int64_t nz_n, const int32
                                                       const int64_t* __restrict__ nz_pos, int64_t nnz,
                                                       const int32_t* __restrict__ col,
                                                       const int32_t* __restrict__ labels, unsigned long long* out) {
-  __shared__ int lbs[kObjThreads / 32][32];
+  __shared__ LbsWarp lbs[kObjThreads / 32];
   __shared__ int64_t scr[33];
   int64_t cnt = 0;
-  lbs_for_each(nz_pos, nz_n, nnz, lbs[threadIdx.x >> 5], [&](bool valid, int64_t j, int64_t k) {
-    if (!valid) return;
-    const int64_t e = __ldg(nz_pos + j) + k;
-    const int32_t u = __ldg(nz_row + j);
-    const int32_t w = __ldg(col + e);
-    cnt += (__ldg(labels + u) == __ldg(labels + w)) ? 1 : 0;
+  // the non-empty rows are contiguous in the CSR, so virtual edge e is CSR entry e
+  lbs_for_each(nz_pos, nz_n, nnz, &lbs[threadIdx.x >> 5], [&](const Lbs& L) {
+    int32_t lu[kLbsK], w[kLbsK];
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      lu[t] = L.ok(t) ? __ldg(labels + __ldg(nz_row + L.item(t))) : 0;
+      w[t] = L.ok(t) ? __ldg(col + L.edge(t)) : 0;
+    }
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t)
+      if (L.ok(t)) cnt += (__ldg(labels + w[t]) == lu[t]) ? 1 : 0;
   });
   cnt = block_sum<int64_t>(cnt, scr);
   if (threadIdx.x == 0 && cnt) atomicAdd(out + 0, (unsigned long long)cnt);
@@ -65,39 +70,52 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
   return z ^ (z >> 33);
 }
 
-// One warp per row: range, order, self loops, degree; symmetry by comparing
-// two hash sums of the pairs (min, max) seen from the lower and from the upper
-// endpoint (equal multisets give equal sums).
-__global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
-                           int* flags, unsigned long long* sums) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+// Offsets: monotone, inside [0, nnz]; largest degree.
+__global__ void k_validate_offsets(int64_t n, int64_t nnz, const int64_t* __restrict__ off, int* flags) {
+  int dmax = 0;
+  for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = off[u], b = off[u + 1];
+    if (a < 0 || b < a || b > nnz) { atomicCAS(flags, 0, kBadOffsets); continue; }
+    const int64_t d = b - a;
+    dmax = max(dmax, d > 0x7FFFFFFF ? 0x7FFFFFFF : (int)d);
+  }
+  dmax = warp_max(dmax);
+  if ((threadIdx.x & 31) == 0 && dmax > 0) atomicMax(flags + 1, dmax);
+}
+
+// Entries, edge-balanced over the non-empty rows: range, order, self loops;
+// symmetry by comparing two hash sums of the pairs (min, max) seen from the
+// lower and from the upper endpoint (equal multisets give equal sums).
+constexpr int kValThreads = 512;
+
+__global__ void __launch_bounds__(kValThreads) k_validate_edges(int64_t n, int64_t nnz, int64_t nz_n,
+                                                               const int32_t* __restrict__ nz_row,
+                                                               const int64_t* __restrict__ nz_pos,
+                                                               const int32_t* __restrict__ col, int* flags,
+                                                               unsigned long long* sums) {
+  __shared__ LbsWarp lbs[kValThreads / 32];
   unsigned long long lo1 = 0, lo2 = 0, up1 = 0, up2 = 0;
   long long nlo = 0, nup = 0;
-  for (int64_t u = gw; u < n; u += nw) {
-    const int64_t a = off[u], b = off[u + 1];
-    if (a < 0 || b < a || b > nnz) {
-      if (lane == 0) atomicCAS(flags, 0, kBadOffsets);
-      continue;
-    }
-    if (lane == 0) {
-      const int64_t d = b - a;
-      atomicMax(flags + 1, d > 0x7FFFFFFF ? 0x7FFFFFFF : (int)d);
-    }
-    for (int64_t e = a + lane; e < b; e += 32) {
-      const int32_t w = col[e];
-      if (w < 0 || w >= n) { atomicCAS(flags, 0, kBadColumn); continue; }
-      if (w == u) { atomicCAS(flags, 0, kSelfLoop); continue; }
-      if (e > a && col[e - 1] >= w) atomicCAS(flags, 0, kUnsorted);
+  int bad = 0;
+  lbs_for_each(nz_pos, nz_n, nnz, &lbs[threadIdx.x >> 5], [&](const Lbs& L) {
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      if (!L.ok(t)) continue;
+      const int64_t e = L.edge(t);
+      const int32_t u = __ldg(nz_row + L.item(t));
+      const int32_t w = __ldg(col + e);
+      if (w < 0 || w >= n) { bad = bad ? bad : kBadColumn; continue; }
+      if (w == u) { bad = bad ? bad : kSelfLoop; continue; }
+      if (L.in_row(t) > 0 && __ldg(col + e - 1) >= w) bad = bad ? bad : kUnsorted;
       const uint64_t key = u < w ? (((uint64_t)u << 32) | (uint32_t)w) : (((uint64_t)w << 32) | (uint32_t)u);
       const uint64_t h1 = mix64(key ^ 0x9E3779B97F4A7C15ull), h2 = mix64(key + 0x632BE59BD9B4E019ull);
       if (u < w) { lo1 += h1; lo2 += h2; ++nlo; } else { up1 += h1; up2 += h2; ++nup; }
     }
-  }
+  });
+  if (bad) atomicCAS(flags, 0, bad);
   lo1 = warp_sum(lo1); lo2 = warp_sum(lo2); up1 = warp_sum(up1); up2 = warp_sum(up2);
   nlo = warp_sum(nlo); nup = warp_sum(nup);
-  if (lane == 0) {
+  if ((threadIdx.x & 31) == 0) {
     atomicAdd(sums + 0, lo1); atomicAdd(sums + 1, lo2);
     atomicAdd(sums + 2, up1); atomicAdd(sums + 3, up2);
     atomicAdd(sums + 4, (unsigned long long)nlo); atomicAdd(sums + 5, (unsigned long long)nup);
@@ -106,7 +124,11 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ o
 
 __global__ void k_validate_finish(int64_t n, const int64_t* __restrict__ off, int64_t nnz, int* flags,
                                   const unsigned long long* sums) {
+  (void)sums;
   if (off[0] != 0 || off[n] != nnz) atomicCAS(flags, 0, kBadOffsets);
+}
+
+__global__ void k_validate_symmetry(int* flags, const unsigned long long* sums) {
   if (sums[0] != sums[2] || sums[1] != sums[3] || sums[4] != sums[5]) atomicCAS(flags, 0, kAsymmetric);
 }
 
@@ -185,14 +207,23 @@ cudaError_t launch_disagreements(int64_t n, int64_t nnz, const int64_t* off, con
 
 size_t validate_workspace_bytes() { return align_up(8 * sizeof(unsigned long long)) + align_up(2 * sizeof(int)); }
 
-cudaError_t launch_validate(int64_t n, int64_t nnz, const int64_t* off, const int32_t* col, void* ws,
-                            int num_sms, cudaStream_t stream) {
-  unsigned long long* sums = static_cast<unsigned long long*>(ws);
+cudaError_t launch_validate_offsets(int64_t n, int64_t nnz, const int64_t* off, void* ws, int num_sms,
+                                    cudaStream_t stream) {
   int* flags = reinterpret_cast<int*>(static_cast<char*>(ws) + align_up(8 * sizeof(unsigned long long)));
   cudaError_t e = cudaMemsetAsync(ws, 0, validate_workspace_bytes(), stream);
   if (e != cudaSuccess) return e;
-  if (n > 0) k_validate<<<num_sms * 8, 256, 0, stream>>>(n, nnz, off, col, flags, sums);
-  k_validate_finish<<<1, 1, 0, stream>>>(n, off, nnz, flags, sums);
+  if (n > 0) k_validate_offsets<<<num_sms * 8, 256, 0, stream>>>(n, nnz, off, flags);
+  k_validate_finish<<<1, 1, 0, stream>>>(n, off, nnz, flags, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_edges(int64_t n, int64_t nnz, const int32_t* nz_row, const int64_t* nz_pos,
+                                  int64_t nz_n, const int32_t* col, void* ws, int num_sms, cudaStream_t stream) {
+  unsigned long long* sums = static_cast<unsigned long long*>(ws);
+  int* flags = reinterpret_cast<int*>(static_cast<char*>(ws) + align_up(8 * sizeof(unsigned long long)));
+  if (nnz > 0)
+    k_validate_edges<<<num_sms * 2, kValThreads, 0, stream>>>(n, nnz, nz_n, nz_row, nz_pos, col, flags, sums);
+  k_validate_symmetry<<<1, 1, 0, stream>>>(flags, sums);
   return cudaGetLastError();
 }
 

@@ -55,27 +55,33 @@ __device__ __forceinline__ unsigned long long word(int32_t hi, uint32_t lo) {
 template <class T>
 __device__ __forceinline__ T vload(const T* p) { return *reinterpret_cast<const volatile T*>(p); }
 
+// Shared memory of one block (dynamic: larger than the 48 KB static limit).
 struct Shared {
   unsigned gen;
   int leader, ok;
   int64_t scr[33];
-  int lbs[kWarps][32];
+  int64_t bcast[2];
   int32_t hist[kHist];
+  LbsWarp lbs[kWarps];
+  AppendBuf app[kWarps];
 };
 
-// Per-thread tallies carried through a round.
+// Per-thread tallies of one round (flushed at every round end).
 struct Tally {
-  long long centers, attached, noncenter, blocked, edges;
-  unsigned long long mc, mm, pairs;
+  int32_t centers, attached, noncenter, blocked;
+  uint32_t mc, mm;              // member-center and member-member edges
+  unsigned long long pairs;     // growth of sum_c C(s_c, 2)
 };
 
 struct K {
   const RoundBuffers& B;
   Ctl* C;
-  volatile Ctl* V;     // plain control-block fields, always read at L2
   Shared* S;
   unsigned G;
   Tally t;
+
+  // plain control-block fields, always accessed at L2
+  __device__ __forceinline__ volatile Ctl* vc() const { return C; }
 
   // ---------------- degree-count table --------------------------------------
   __device__ void hist_add(int32_t th, uint32_t d, int delta) {
@@ -97,11 +103,40 @@ struct K {
   }
 
   // ---------------- barrier --------------------------------------------------
-  __device__ bool arrive() { return bar_arrive(reinterpret_cast<GridBarrier*>(&C->bar), G, &S->gen, &S->leader); }
+  // Arrive at a grid barrier; the leader books the time since the previous
+  // barrier to phase category `cat` (a cheap always-on profile of the rounds).
+  __device__ bool arrive(int cat) {
+    const bool lead = bar_arrive(reinterpret_cast<GridBarrier*>(&C->bar), G, &S->gen, &S->leader);
+    if (lead && threadIdx.x == 0) {
+      const unsigned long long now = globaltimer_ns();
+      vc()->ph_ns[cat] += now - vc()->ph_t0;
+      vc()->ph_t0 = now;
+    }
+    return lead;
+  }
   __device__ bool finish(bool lead) {
     return bar_finish(reinterpret_cast<GridBarrier*>(&C->bar), lead, &S->gen, &C->err, &S->ok);
   }
   __device__ void fail(int code) { atomicCAS(&C->err, kOk, code); }
+
+  __device__ RowList new_list() const { return RowList{B.new_v, B.new_e, B.new_d, nullptr, &C->new_pack}; }
+  __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, nullptr, &C->blk_pack}; }
+  __device__ LbsWarp* lbs_ws() const { return &S->lbs[threadIdx.x >> 5]; }
+  __device__ AppendBuf* app_buf() const { return &S->app[threadIdx.x >> 5]; }
+
+  // Pair tally of cluster growth: a member joining the cluster of center rank
+  // c adds (current size) new pairs, sum_c C(s_c, 2) in total.  Lanes with the
+  // same c share one atomic.
+  __device__ void add_member(bool want, int32_t c) {
+    const int lane = threadIdx.x & 31;
+    const int key = want ? c : -1;
+    const unsigned grp = __match_any_sync(FULL, key);
+    const int leader = __ffs(grp) - 1;
+    int old = 0;
+    if (want && lane == leader) old = atomicAdd(B.size + c, __popc(grp));
+    old = __shfl_sync(FULL, old, leader);
+    if (want) t.pairs += 1ull + (unsigned long long)(old + __popc(grp & ((1u << lane) - 1u)));
+  }
 
   __device__ int32_t al_at(int sel, int identity, int64_t i) const {
     if (identity) return (int32_t)i;
@@ -145,51 +180,56 @@ struct K {
   __device__ void plan_round() {
     __shared__ int s_dec;
     if (threadIdx.x == 0) {
-      const int64_t n_alive = V->n_alive;
+      const int64_t n_alive = vc()->n_alive;
       int dec = 0;
-      if (n_alive <= 0) { V->done = 1; dec = 1; }
-      else if (!V->al_identity && V->al_len - V->cursor > 4 * n_alive + 65536) { V->need_rebuild = 1; dec = 1; }
+      if (n_alive <= 0) { vc()->done = 1; dec = 1; }
+      else if (!vc()->al_identity && vc()->al_len - vc()->cursor > 4 * n_alive + 65536) { vc()->need_rebuild = 1; dec = 1; }
       s_dec = dec;
     }
     __syncthreads();
     if (s_dec) return;
     // walk the degree table down from `top`
-    const int32_t th = V->th;
-    int32_t t = V->top;
+    const int32_t th = vc()->th;
+    int32_t t = vc()->top;
     int32_t found = -1;
     while (t >= th) {
-      const int32_t d = t - (int32_t)threadIdx.x;
-      const int32_t hit = (d >= th && ldcg(B.cnt + d) > 0) ? d : -1;
+      // four bins per thread per step: t, t-1, ... t-4*blockDim+1
+      int32_t hit = -1;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int32_t d = t - (int32_t)(threadIdx.x * 4 + q);
+        if (d >= th && hit < 0 && ldcg(B.cnt + d) > 0) hit = d;
+      }
       found = (int32_t)block_max<int64_t>(hit, S->scr);
       if (found >= 0) break;
-      t -= (int32_t)blockDim.x;
+      t -= 4 * (int32_t)blockDim.x;
     }
     if (threadIdx.x == 0) {
       int32_t delta;
-      if (found >= 0) { delta = found; V->top = found; }
-      else if (th <= 1) { delta = 0; V->top = 0; }
-      else { V->need_rebuild = 1; s_dec = 1; }
+      if (found >= 0) { delta = found; vc()->top = found; }
+      else if (th <= 1) { delta = 0; vc()->top = 0; }
+      else { vc()->need_rebuild = 1; s_dec = 1; }
       if (!s_dec) {
-        const int64_t n_alive = V->n_alive;
+        const int64_t n_alive = vc()->n_alive;
         int64_t k;
         if (delta <= 0) k = n_alive;
         else {
-          const unsigned long long num = (unsigned long long)V->eps_ppm * (unsigned long long)n_alive;
+          const unsigned long long num = (unsigned long long)vc()->eps_ppm * (unsigned long long)n_alive;
           const unsigned long long den = 1000000ull * (unsigned long long)delta;
           k = (int64_t)((num + den - 1) / den);
           if (k < 1) k = 1;
           if (k > n_alive) k = n_alive;
         }
-        V->delta = delta;
-        V->k = k;
-        V->need = k;
-        V->win_lo = V->cursor;
-        const int64_t avail = V->al_len - V->cursor;
+        vc()->delta = delta;
+        vc()->k = k;
+        vc()->need = k;
+        vc()->win_lo = vc()->cursor;
+        const int64_t avail = vc()->al_len - vc()->cursor;
         const int64_t est = (int64_t)((double)k * (double)avail / (double)n_alive * 1.05) + 256;
-        V->win_len = est < avail ? est : avail;
-        V->act_pack = 0; V->new_pack = 0; V->blk_pack = 0;
-        V->r_centers = 0; V->r_attached = 0; V->r_noncenter = 0; V->r_blocked = 0; V->r_edges = 0;
-        V->r0 = -1;
+        vc()->win_len = est < avail ? est : avail;
+        vc()->act_pack = 0; vc()->new_pack = 0; vc()->blk_pack = 0;
+        vc()->r_centers = 0; vc()->r_attached = 0; vc()->r_noncenter = 0; vc()->r_blocked = 0; vc()->r_edges = 0;
+        vc()->r0 = -1;
       }
     }
     __syncthreads();
@@ -216,16 +256,16 @@ struct K {
     cnt = block_sum<int64_t>(cnt, S->scr);
     mx = block_max<int64_t>(mx, S->scr);
     if (threadIdx.x == 0) { B.blk_a[blockIdx.x] = cnt; B.blk_b[blockIdx.x] = mx; }
-    bool lead = arrive();
+    bool lead = arrive(0);
     if (lead) {
       const int64_t tot = leader_prefix_blocks();
       const int64_t D = leader_max_blocks();
       if (threadIdx.x == 0) {
-        if (tot != V->n_alive) fail(kErrInternal);
-        V->take = tot;                 // new list length
-        V->top = (int32_t)D;
+        if (tot != vc()->n_alive) fail(kErrInternal);
+        vc()->take = tot;                 // new list length
+        vc()->top = (int32_t)D;
         const int32_t th = (int32_t)(D >> 2);
-        V->th = th < 1 ? 1 : th;
+        vc()->th = th < 1 ? 1 : th;
       }
     }
     if (!finish(lead)) return false;
@@ -252,18 +292,18 @@ struct K {
       run += tot;
     }
     hist_flush(th);
-    lead = arrive();
+    lead = arrive(1);
     if (lead) {
       if (threadIdx.x == 0) {
-        V->al_sel = sel ^ 1;
-        V->al_identity = 0;
-        V->al_len = V->take;
-        V->cursor = 0;
-        V->need_rebuild = 0;
+        vc()->al_sel = sel ^ 1;
+        vc()->al_identity = 0;
+        vc()->al_len = vc()->take;
+        vc()->cursor = 0;
+        vc()->need_rebuild = 0;
         // a rebuild always leaves a tracked vertex (or Delta = 0), so two in a
         // row without a round in between mean the table is inconsistent
-        V->rebuilds_in_row += 1;
-        if (V->rebuilds_in_row > 2) fail(kErrInternal);
+        vc()->rebuilds_in_row += 1;
+        if (vc()->rebuilds_in_row > 2) fail(kErrInternal);
       }
       __syncthreads();
       plan_round();
@@ -272,10 +312,12 @@ struct K {
   }
 
   // ---------------- active-set selection (Alg. 2: A = next k alive of pi) ----
-  __device__ void emit_active(int32_t v, int32_t r, int algo, int32_t th, bool want) {
+  // Called by every thread of the block for one tile of the window; threads
+  // with want == true hold an active vertex v of rank r.
+  __device__ void emit_actives(int32_t v, int32_t r, int algo, int32_t th, bool want) {
     uint32_t d = 0;
     int64_t deg0 = 0, row = 0;
-    bool listed = false;
+    int64_t listed = 0;
     if (want) {
       const unsigned long long x = ldcg(B.st + v);
       d = lo_of(x);
@@ -288,18 +330,30 @@ struct K {
         row = __ldg(B.off + v);
         deg0 = __ldg(B.off + v + 1) - row;
         B.st[v] = word(~r, algo == kAlgoCW ? kCenter : kUndecided);
-        listed = true;
+        listed = 1;
+        if (algo == kAlgoCW) t.centers += 1;
       }
     }
-    int64_t j = 0, ep = 0;
-    warp_append_packed(listed, deg0, &C->act_pack, &j, &ep);
+    // one atomic per block and tile on the packed list counter
+    int64_t cnt_tot, e_tot;
+    const int64_t jx = block_exclusive_sum<int64_t>(listed, S->scr, &cnt_tot);
+    const int64_t ex = block_exclusive_sum<int64_t>(listed ? deg0 : 0, S->scr, &e_tot);
+    if (cnt_tot == 0) return;
+    if (threadIdx.x == 0) {
+      const unsigned long long old =
+          atomicAdd(&C->act_pack, ((unsigned long long)cnt_tot << kPackShift) | (unsigned long long)e_tot);
+      S->bcast[0] = (int64_t)(old >> kPackShift);
+      S->bcast[1] = (int64_t)(old & kPackEdgeMask);
+    }
+    __syncthreads();
+    const int64_t j = S->bcast[0] + jx, ep = S->bcast[1] + ex;
+    __syncthreads();
     if (listed) {
       B.act_v[j] = v;
       B.act_r[j] = r;
       B.act_e[j] = ep;
-      B.act_row[j] = row;
+      B.act_d[j] = row - ep;
       B.blk_flag[j] = 0;
-      if (algo == kAlgoCW) t.centers += 1;
     }
   }
 
@@ -317,12 +371,12 @@ struct K {
       }
       cnt = block_sum<int64_t>(cnt, S->scr);
       if (threadIdx.x == 0) B.blk_a[blockIdx.x] = cnt;
-      bool lead = arrive();
+      bool lead = arrive(2);
       if (lead) {
         const int64_t tot = leader_prefix_blocks();
         if (threadIdx.x == 0) {
-          const int64_t need = V->need;
-          V->take = tot < need ? tot : need;
+          const int64_t need = vc()->need;
+          vc()->take = tot < need ? tot : need;
         }
       }
       if (!finish(lead)) return false;
@@ -344,33 +398,35 @@ struct K {
           int64_t tot;
           const int64_t g = run + block_exclusive_sum<int64_t>(alive, S->scr, &tot);
           const bool want = alive && g < take;
-          if (want && g == 0 && first_window) V->r0 = r;
-          if (want && take == need && g == take - 1) V->cursor_next = i + 1;
-          emit_active(v, r, algo, th, want);
+          if (want && g == 0 && first_window) vc()->r0 = r;
+          if (want && take == need && g == take - 1) vc()->cursor_next = i + 1;
+          emit_actives(v, r, algo, th, want);
           run += tot;
           if (run >= take) break;           // uniform across the block
         }
       }
       hist_flush(th);
-      lead = arrive();
+      lead = arrive(3);
       if (lead && threadIdx.x == 0) {
-        const int64_t left = V->need - V->take;
-        V->need = left;
+        const int64_t left = vc()->need - vc()->take;
+        vc()->need = left;
         if (left == 0) {
-          V->cursor = V->cursor_next;
-          const unsigned long long p = V->act_pack;
-          V->act_n = (int64_t)(p >> kPackShift);
-          V->act_E = (int64_t)(p & kPackEdgeMask);
+          vc()->cursor = vc()->cursor_next;
+          const unsigned long long p = vc()->act_pack;
+          vc()->act_n = (int64_t)(p >> kPackShift);
+          vc()->act_E = (int64_t)(p & kPackEdgeMask);
+          // adjacency passes over the active rows: attach (and C4 detection)
+          vc()->r_edges = vc()->act_E * (vc()->algo == kAlgoC4 ? 2 : 1);
         } else {
-          const int64_t lo2 = V->win_lo + V->win_len;
-          const int64_t avail = V->al_len - lo2;
-          const int64_t alive_left = V->n_alive - (V->k - left);
+          const int64_t lo2 = vc()->win_lo + vc()->win_len;
+          const int64_t avail = vc()->al_len - lo2;
+          const int64_t alive_left = vc()->n_alive - (vc()->k - left);
           if (avail <= 0 || alive_left <= 0) {
             fail(kErrInternal);
           } else {
             const int64_t est = (int64_t)((double)left * (double)avail / (double)alive_left * 1.1) + 1024;
-            V->win_lo = lo2;
-            V->win_len = est < avail ? est : avail;
+            vc()->win_lo = lo2;
+            vc()->win_len = est < avail ? est : avail;
           }
         }
       }
@@ -380,76 +436,80 @@ struct K {
   }
 
   // ---------------- createCluster: push a center's rank to its neighbours ----
-  // Lanes with `push` set try to attach u to the center of rank r.
-  __device__ void attach_lanes(bool push, int32_t u, int32_t r, int32_t th) {
+  // Lanes with push == true try to attach u (state word x, read earlier) to
+  // the center of rank r.  All 32 lanes must call it.
+  __device__ void attach_one(bool push, int32_t u, int32_t r, unsigned long long x, int32_t th) {
     bool fresh = false;
     uint32_t d_old = 0;
-    if (push) {
-      const unsigned long long nv = (unsigned long long)(uint32_t)r << 32;
-      const unsigned long long x = ldcg(B.st + u);
-      if ((long long)x > (long long)nv) {
-        const unsigned long long old =
-            (unsigned long long)atomicMin(reinterpret_cast<long long*>(B.st + u), (long long)nv);
-        if (hi_of(old) == kAliveHi) { fresh = true; d_old = lo_of(old); }
-      }
+    const unsigned long long nv = (unsigned long long)(uint32_t)r << 32;
+    if (push && (long long)x > (long long)nv) {
+      const unsigned long long old =
+          (unsigned long long)atomicMin(reinterpret_cast<long long*>(B.st + u), (long long)nv);
+      if (hi_of(old) == kAliveHi) { fresh = true; d_old = lo_of(old); }
     }
-    bool want = false;
-    int64_t deg0 = 0, row = 0;
     if (fresh) {
       hist_add(th, d_old, -1);
       t.attached += 1;
-      if (d_old == 1) {
-        // the center is u's only alive neighbour: nothing to decrement, and
-        // no other center can reach u, so the label is already final
-        t.mc += 1;
-        t.pairs += 1ull + (unsigned long long)atomicAdd(B.size + r, 1);
-      } else {
-        row = __ldg(B.off + u);
-        deg0 = __ldg(B.off + u + 1) - row;
-        want = true;
-      }
     }
-    int64_t j = 0, ep = 0;
-    warp_append_packed(want, deg0, &C->new_pack, &j, &ep);
+    // The center is the only alive neighbour of a fresh vertex of residual
+    // degree 1: nothing to decrement, and no other center can reach it, so
+    // its label is already final.
+    const bool single = fresh && d_old == 1;
+    if (single) t.mc += 1;
+    add_member(single, r);
+    const bool want = fresh && d_old != 1;
+    int64_t row = 0;
+    int32_t len = 0;
     if (want) {
-      B.new_v[j] = u;
-      B.new_e[j] = ep;
-      B.new_row[j] = row;
+      row = __ldg(B.off + u);
+      len = (int32_t)(__ldg(B.off + u + 1) - row);
     }
+    append_stage(app_buf(), want, u, row, len, new_list());
   }
 
   __device__ void attach_from_actives(bool skip_blocked, int32_t th) {
     const int64_t an = vload(&C->act_n), aE = vload(&C->act_E);
-    int* wb = S->lbs[threadIdx.x >> 5];
-    lbs_for_each(B.act_e, an, aE, wb, [&](bool valid, int64_t j, int64_t k) {
-      bool push = false;
-      int32_t u = 0, r = 0;
-      if (valid) {
-        t.edges += 1;
-        if (!skip_blocked || ldcg(B.blk_flag + j) == 0) {
-          r = ldcg(B.act_r + j);
-          u = __ldg(B.col + ldcg(B.act_row + j) + k);
-          push = true;
-        }
+    lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
+      bool push[kLbsK];
+      int32_t r[kLbsK], u[kLbsK];
+      int64_t pos[kLbsK];
+      unsigned long long x[kLbsK];
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) {
+        push[q] = L.ok(q) && (!skip_blocked || ldcg(B.blk_flag + L.item(q)) == 0);
+        r[q] = push[q] ? ldcg(B.act_r + L.item(q)) : 0;
+        pos[q] = push[q] ? L.edge(q) + ldcg(B.act_d + L.item(q)) : 0;
       }
-      attach_lanes(push, u, r, th);
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) u[q] = push[q] ? __ldg(B.col + pos[q]) : 0;
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) x[q] = push[q] ? ldcg(B.st + u[q]) : 0;
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) attach_one(push[q], u[q], r[q], x[q], th);
     });
+    append_flush(app_buf(), new_list());
   }
 
   // ---------------- C4: blocked detection ------------------------------------
   __device__ void c4_detect() {
     const int64_t an = vload(&C->act_n), aE = vload(&C->act_E);
     const int32_t r0 = vload(&C->r0);
-    int* wb = S->lbs[threadIdx.x >> 5];
-    lbs_for_each(B.act_e, an, aE, wb, [&](bool valid, int64_t j, int64_t k) {
-      if (!valid) return;
-      t.edges += 1;
-      const int32_t rv = ldcg(B.act_r + j);
-      const int32_t u = __ldg(B.col + ldcg(B.act_row + j) + k);
-      const int32_t hw = hi_of(ldcg(B.st + u));
-      if (hw < 0) {
-        const int32_t ru = ~hw;
-        if (ru >= r0 && ru < rv) B.blk_flag[j] = 1;   // an earlier active neighbour: v must wait
+    lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
+      int32_t rv[kLbsK], u[kLbsK];
+      int64_t pos[kLbsK];
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) {
+        rv[q] = L.ok(q) ? ldcg(B.act_r + L.item(q)) : 0;
+        pos[q] = L.ok(q) ? L.edge(q) + ldcg(B.act_d + L.item(q)) : 0;
+      }
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) u[q] = L.ok(q) ? __ldg(B.col + pos[q]) : 0;
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) {
+        if (!L.ok(q)) continue;
+        const int32_t hw = hi_of(ldcg(B.st + u[q]));
+        // an earlier active neighbour: v must wait (isCenter)
+        if (hw < 0 && ~hw >= r0 && ~hw < rv[q]) B.blk_flag[L.item(q)] = 1;
       }
     });
   }
@@ -463,27 +523,30 @@ struct K {
     for (int64_t base = gw * 32; base < an; base += nw * 32) {
       const int64_t j = base + lane;
       bool blocked = false;
-      int64_t deg0 = 0;
+      int64_t len = 0, row = 0;
       if (j < an) {
         const int32_t v = ldcg(B.act_v + j), r = ldcg(B.act_r + j);
         if (ldcg(B.blk_flag + j)) {
           blocked = true;
-          deg0 = __ldg(B.off + v + 1) - __ldg(B.off + v);
+          row = ldcg(B.act_e + j) + ldcg(B.act_d + j);
+          len = __ldg(B.off + v + 1) - __ldg(B.off + v);
           t.blocked += 1;
         } else {
           B.st[v] = word(~r, kCenter);
           t.centers += 1;
         }
       }
-      int64_t q = 0, ep = 0;
-      warp_append_packed(blocked, deg0, &C->blk_pack, &q, &ep);
-      if (blocked) {
-        B.b_j[q] = (int32_t)j;
-        B.b_e[q] = ep;
-        B.hit_c[q] = 0;
-        B.hit_p[q] = 0;
-        B.pull[q] = 0x7FFFFFFF;
-      }
+      warp_append_rows(blocked, (int32_t)j, row, len, 0, blk_list());
+    }
+  }
+
+  // Reset the per-item scratch of the blocked list (after its counter is known).
+  __device__ void c4_blocked_init() {
+    const int64_t bn = vload(&C->b_n);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
+      B.hit_c[q] = 0;
+      B.hit_p[q] = 0;
+      B.pull[q] = 0x7FFFFFFF;
     }
   }
 
@@ -492,22 +555,20 @@ struct K {
   __device__ void c4_fix_scan() {
     const int64_t bn = vload(&C->b_n), bE = vload(&C->b_E);
     const int32_t r0 = vload(&C->r0);
-    int* wb = S->lbs[threadIdx.x >> 5];
-    lbs_for_each(B.b_e, bn, bE, wb, [&](bool valid, int64_t q, int64_t k) {
-      if (!valid) return;
-      const int32_t j = ldcg(B.b_j + q);
-      const int32_t v = ldcg(B.act_v + j), rv = ldcg(B.act_r + j);
-      if (lo_of(ldcg(B.st + v)) != kUndecided) return;
-      t.edges += 1;
-      const int32_t u = __ldg(B.col + ldcg(B.act_row + j) + k);
-      const unsigned long long x = ldcg(B.st + u);
-      const int32_t hw = hi_of(x);
-      if (hw < 0) {
-        const int32_t ru = ~hw;
-        if (ru >= r0 && ru < rv) {
+    lbs_for_each(B.b_e, bn, bE, lbs_ws(), [&](const Lbs& L) {
+#pragma unroll
+      for (int i = 0; i < kLbsK; ++i) {
+        if (!L.ok(i)) continue;
+        const int32_t j = ldcg(B.b_j + L.item(i));
+        const int32_t v = ldcg(B.act_v + j), rv = ldcg(B.act_r + j);
+        if (lo_of(ldcg(B.st + v)) != kUndecided) continue;
+        const int32_t u = __ldg(B.col + L.edge(i) + ldcg(B.b_d + L.item(i)));
+        const unsigned long long x = ldcg(B.st + u);
+        const int32_t hw = hi_of(x);
+        if (hw < 0 && ~hw >= r0 && ~hw < rv) {
           const uint32_t su = lo_of(x);
-          if (su == kCenter) B.hit_c[q] = 1;
-          else if (su == kUndecided) B.hit_p[q] = 1;
+          if (su == kCenter) B.hit_c[L.item(i)] = 1;
+          else if (su == kUndecided) B.hit_p[L.item(i)] = 1;
         }
       }
     });
@@ -535,27 +596,29 @@ struct K {
   __device__ void c4_blocked_attach(int32_t th) {
     const int64_t bn = vload(&C->b_n), bE = vload(&C->b_E);
     const int32_t r0 = vload(&C->r0);
-    int* wb = S->lbs[threadIdx.x >> 5];
-    lbs_for_each(B.b_e, bn, bE, wb, [&](bool valid, int64_t q, int64_t k) {
-      bool push = false;
-      int32_t u = 0, r = 0;
-      if (valid) {
-        t.edges += 1;
-        const int32_t j = ldcg(B.b_j + q);
-        const int32_t v = ldcg(B.act_v + j);
-        r = ldcg(B.act_r + j);
-        u = __ldg(B.col + ldcg(B.act_row + j) + k);
-        const uint32_t sv = lo_of(ldcg(B.st + v));
-        if (sv == kCenter) {
-          push = true;
-        } else {
-          const unsigned long long x = ldcg(B.st + u);
-          const int32_t hw = hi_of(x);
-          if (hw < 0 && ~hw >= r0 && lo_of(x) == kCenter) atomicMin(B.pull + q, ~hw);
+    lbs_for_each(B.b_e, bn, bE, lbs_ws(), [&](const Lbs& L) {
+#pragma unroll
+      for (int i = 0; i < kLbsK; ++i) {
+        bool push = false;
+        int32_t u = 0, r = 0;
+        unsigned long long x = 0;
+        if (L.ok(i)) {
+          const int32_t j = ldcg(B.b_j + L.item(i));
+          const int32_t v = ldcg(B.act_v + j);
+          r = ldcg(B.act_r + j);
+          u = __ldg(B.col + L.edge(i) + ldcg(B.b_d + L.item(i)));
+          x = ldcg(B.st + u);
+          if (lo_of(ldcg(B.st + v)) == kCenter) {
+            push = true;
+          } else {
+            const int32_t hw = hi_of(x);
+            if (hw < 0 && ~hw >= r0 && lo_of(x) == kCenter) atomicMin(B.pull + L.item(i), ~hw);
+          }
         }
+        attach_one(push, u, r, x, th);
       }
-      attach_lanes(push, u, r, th);
     });
+    append_flush(app_buf(), new_list());
   }
 
   // C4: a non-center active takes its pulled label and joins the removal list.
@@ -568,7 +631,7 @@ struct K {
       const int64_t q = base + lane;
       bool want = false;
       int32_t v = 0;
-      int64_t deg0 = 0, row = 0;
+      int64_t len = 0, row = 0;
       if (q < bn) {
         const int32_t j = ldcg(B.b_j + q);
         v = ldcg(B.act_v + j);
@@ -577,18 +640,12 @@ struct K {
           if (lab == 0x7FFFFFFF) fail(kErrInternal);   // a non-center always has a center neighbour
           B.st[v] = word(lab, 0);
           t.noncenter += 1;
-          row = __ldg(B.off + v);
-          deg0 = __ldg(B.off + v + 1) - row;
+          row = ldcg(B.b_e + q) + ldcg(B.b_d + q);
+          len = __ldg(B.off + v + 1) - __ldg(B.off + v);
           want = true;
         }
       }
-      int64_t j2 = 0, ep = 0;
-      warp_append_packed(want, deg0, &C->new_pack, &j2, &ep);
-      if (want) {
-        B.new_v[j2] = v;
-        B.new_e[j2] = ep;
-        B.new_row[j2] = row;
-      }
+      warp_append_rows(want, v, row, len, 0, new_list());
     }
   }
 
@@ -596,58 +653,73 @@ struct K {
   __device__ void decrement(int32_t th) {
     const unsigned long long p = vload(&C->new_pack);
     const int64_t nn = (int64_t)(p >> kPackShift), nE = (int64_t)(p & kPackEdgeMask);
-    int* wb = S->lbs[threadIdx.x >> 5];
-    lbs_for_each(B.new_e, nn, nE, wb, [&](bool valid, int64_t j, int64_t k) {
-      if (!valid) return;
-      t.edges += 1;
-      const int32_t u = ldcg(B.new_v + j);
-      const int32_t lu = hi_of(ldcg(B.st + u));
-      if (k == 0) t.pairs += 1ull + (unsigned long long)atomicAdd(B.size + lu, 1);
-      const int32_t w = __ldg(B.col + ldcg(B.new_row + j) + k);
-      const unsigned long long x = ldcg(B.st + w);
-      const int32_t hw = hi_of(x);
-      if (hw == kAliveHi) {
-        const uint32_t d = atomicSub(reinterpret_cast<unsigned*>(B.st + w), 1u);   // low word
-        if (d == 0) { fail(kErrInternal); return; }
-        hist_add(th, d, -1);
-        hist_add(th, d - 1, 1);
-      } else if (decode_label(hw) == lu) {
-        if (hw < 0) t.mc += 1; else t.mm += 1;
+    lbs_for_each(B.new_e, nn, nE, lbs_ws(), [&](const Lbs& L) {
+      int32_t u[kLbsK], w[kLbsK], lu[kLbsK];
+      int64_t pos[kLbsK];
+      unsigned long long x[kLbsK];
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) {
+        u[q] = L.ok(q) ? ldcg(B.new_v + L.item(q)) : 0;
+        pos[q] = L.ok(q) ? L.edge(q) + ldcg(B.new_d + L.item(q)) : 0;
+      }
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) w[q] = L.ok(q) ? __ldg(B.col + pos[q]) : 0;
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) {
+        lu[q] = L.ok(q) ? hi_of(ldcg(B.st + u[q])) : 0;
+        x[q] = L.ok(q) ? ldcg(B.st + w[q]) : 0;
+      }
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) {
+        add_member(L.ok(q) && L.in_row(q) == 0, lu[q]);   // once per removed member
+        if (!L.ok(q)) continue;
+        const int32_t hw = hi_of(x[q]);
+        if (hw == kAliveHi) {
+          const uint32_t d = atomicSub(reinterpret_cast<unsigned*>(B.st + w[q]), 1u);   // low word
+          if (d == 0) { fail(kErrInternal); continue; }
+          hist_add(th, d, -1);
+          hist_add(th, d - 1, 1);
+        } else if (decode_label(hw) == lu[q]) {
+          if (hw < 0) t.mc += 1; else t.mm += 1;
+        }
       }
     });
   }
 
   // Reduce the round tallies of this block into the control block.
   __device__ void flush_round_tallies() {
-    long long v[5] = {t.centers, t.attached, t.noncenter, t.blocked, t.edges};
-    long long* dst[5] = {&C->r_centers, &C->r_attached, &C->r_noncenter, &C->r_blocked, &C->r_edges};
+    const long long v[6] = {t.centers, t.attached, t.noncenter, t.blocked, (long long)t.mc, (long long)t.mm};
+    long long* dst[6] = {&C->r_centers, &C->r_attached, &C->r_noncenter, &C->r_blocked,
+                         reinterpret_cast<long long*>(&C->mc), reinterpret_cast<long long*>(&C->mm)};
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < 6; ++i) {
       const long long s = block_sum<int64_t>(v[i], S->scr);
       if (threadIdx.x == 0 && s != 0) atomicAdd(reinterpret_cast<unsigned long long*>(dst[i]), (unsigned long long)s);
     }
-    t.centers = t.attached = t.noncenter = t.blocked = t.edges = 0;
+    const unsigned long long pr = (unsigned long long)block_sum<int64_t>((int64_t)t.pairs, S->scr);
+    if (threadIdx.x == 0 && pr != 0) atomicAdd(&C->pairs, pr);
+    t = Tally{0, 0, 0, 0, 0, 0, 0};
   }
 
   // Leader at the end of a round: statistics, n_i update, plan the next round.
   __device__ void end_round() {
     if (threadIdx.x == 0) {
-      const int64_t k = V->k;
-      const int64_t removed = k + V->r_attached;
-      const int64_t centers = k - V->r_noncenter;
-      const int64_t r = V->round;
+      const int64_t k = vc()->k;
+      const int64_t removed = k + vc()->r_attached;
+      const int64_t centers = k - vc()->r_noncenter;
+      const int64_t r = vc()->round;
       if (r < B.stats_cap) {
         RoundStat s;
-        s.n_alive = V->n_alive; s.delta = V->delta; s.k = k; s.centers = centers;
-        s.removed = removed; s.blocked = V->r_blocked; s.edges = V->r_edges;
+        s.n_alive = vc()->n_alive; s.delta = vc()->delta; s.k = k; s.centers = centers;
+        s.removed = removed; s.blocked = vc()->r_blocked; s.edges = vc()->r_edges + (int64_t)(vc()->new_pack & kPackEdgeMask);
         B.stats[r] = s;
       }
-      if (V->r_centers != centers) fail(kErrInternal);
-      V->n_alive -= removed;
-      if (V->n_alive < 0) fail(kErrInternal);
-      V->round = r + 1;
-      V->rebuilds_in_row = 0;
-      if (V->round > V->n + 1) fail(kErrInternal);
+      if (vc()->r_centers != centers) fail(kErrInternal);
+      vc()->n_alive -= removed;
+      if (vc()->n_alive < 0) fail(kErrInternal);
+      vc()->round = r + 1;
+      vc()->rebuilds_in_row = 0;
+      if (vc()->round > vc()->n + 1) fail(kErrInternal);
     }
     __syncthreads();
     plan_round();
@@ -655,13 +727,16 @@ struct K {
 };
 
 __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ RoundBuffers B) {
-  __shared__ Shared S;
-  K k{B, B.ctl, B.ctl, &S, gridDim.x, Tally{0, 0, 0, 0, 0, 0, 0, 0}};
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shared& S = *reinterpret_cast<Shared*>(smem_raw);
+  K k{B, B.ctl, &S, gridDim.x, Tally{0, 0, 0, 0, 0, 0, 0}};
   for (int i = threadIdx.x; i < kHist; i += blockDim.x) S.hist[i] = 0;
+  if ((threadIdx.x & 31) == 0) S.app[threadIdx.x >> 5].n = 0;
   __syncthreads();
   Ctl* C = B.ctl;
   volatile Ctl* V = B.ctl;
   const int algo = V->algo;
+  if (blockIdx.x == 0 && threadIdx.x == 0) V->ph_t0 = globaltimer_ns();
 
   for (;;) {
     if (vload(&C->need_rebuild)) {
@@ -675,64 +750,60 @@ __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ 
     if (algo == kAlgoCW) {
       k.attach_from_actives(false, th);
       k.hist_flush(th);
-      lead = k.arrive();
+      lead = k.arrive(4);
       if (!k.finish(lead)) return;
     } else {
       k.c4_detect();
-      lead = k.arrive();
+      lead = k.arrive(4);
       if (!k.finish(lead)) return;
       k.c4_classify();
       k.attach_from_actives(true, th);
       k.hist_flush(th);
-      lead = k.arrive();
+      lead = k.arrive(4);
       if (lead && threadIdx.x == 0) {
         const unsigned long long p = V->blk_pack;
         V->b_n = (int64_t)(p >> kPackShift);
         V->b_E = (int64_t)(p & kPackEdgeMask);
         V->undecided = V->b_n;
         V->fix_iter = 0;
+        V->r_edges += 2 * V->b_E;          // blocked attach / pull pass, first fixpoint scan
       }
       if (!k.finish(lead)) return;
       if (vload(&C->b_n) > 0) {
+        k.c4_blocked_init();
+        lead = k.arrive(5);
+        if (!k.finish(lead)) return;
         while (vload(&C->undecided) > 0) {
           k.c4_fix_scan();
-          lead = k.arrive();
+          lead = k.arrive(5);
           if (lead && threadIdx.x == 0) V->undecided = 0;
           if (!k.finish(lead)) return;
           const long long left = block_sum<int64_t>(k.c4_fix_decide(), S.scr);
           if (threadIdx.x == 0 && left) atomicAdd(reinterpret_cast<unsigned long long*>(&C->undecided),
                                                   (unsigned long long)left);
-          lead = k.arrive();
+          lead = k.arrive(5);
           if (lead && threadIdx.x == 0) {
             V->fix_iter += 1;
+            if (V->fix_iter > 1) V->r_edges += V->b_E;
             if (V->fix_iter > V->b_n + 1) { k.fail(kErrInternal); V->undecided = 0; }
           }
           if (!k.finish(lead)) return;
         }
         k.c4_blocked_attach(th);
         k.hist_flush(th);
-        lead = k.arrive();
+        lead = k.arrive(5);
         if (!k.finish(lead)) return;
         k.c4_pull_finalize();
-        lead = k.arrive();
+        lead = k.arrive(5);
         if (!k.finish(lead)) return;
       }
     }
     k.decrement(th);
     k.hist_flush(th);
     k.flush_round_tallies();
-    lead = k.arrive();
+    lead = k.arrive(6);
     if (lead) k.end_round();
     if (!k.finish(lead)) return;
-  }
-  // objective tallies of the whole run
-  const unsigned long long mc = block_sum<int64_t>((int64_t)k.t.mc, S.scr);
-  const unsigned long long mm = block_sum<int64_t>((int64_t)k.t.mm, S.scr);
-  const unsigned long long pr = block_sum<int64_t>((int64_t)k.t.pairs, S.scr);
-  if (threadIdx.x == 0) {
-    if (mc) atomicAdd(&C->mc, mc);
-    if (mm) atomicAdd(&C->mm, mm);
-    if (pr) atomicAdd(&C->pairs, pr);
   }
 }
 
@@ -784,13 +855,13 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   b += align_up(sizeof(Ctl));
   b += align_up(8 * nn);                 // st
   b += 2 * align_up(4 * nn);             // al0, al1
-  b += 2 * align_up(4 * nn) + 2 * align_up(8 * nn);   // act_v, act_r, act_e, act_row
-  b += align_up(4 * nn) + 2 * align_up(8 * nn);       // new_v, new_e, new_row
+  b += 2 * align_up(4 * nn) + 2 * align_up(8 * nn);   // act_v, act_r, act_e, act_d
+  b += align_up(4 * nn) + 2 * align_up(8 * nn);       // new_v, new_e, new_d
   b += align_up(4 * nn);                 // size
   b += align_up(4 * ((size_t)max_deg + 2 + kHist));   // cnt
   b += 3 * align_up(nn);                 // blk_flag, hit_c, hit_p
   b += align_up(4 * nn);                 // pull
-  b += align_up(4 * nn) + align_up(8 * nn);           // b_j, b_e
+  b += align_up(4 * nn) + 2 * align_up(8 * nn);       // b_j, b_e, b_d
   b += 2 * align_up(8 * ((size_t)grid + 1));          // blk_a, blk_b
   return b;
 }
@@ -806,10 +877,10 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   B->act_v = reinterpret_cast<int32_t*>(take(4 * nn));
   B->act_r = reinterpret_cast<int32_t*>(take(4 * nn));
   B->act_e = reinterpret_cast<int64_t*>(take(8 * nn));
-  B->act_row = reinterpret_cast<int64_t*>(take(8 * nn));
+  B->act_d = reinterpret_cast<int64_t*>(take(8 * nn));
   B->new_v = reinterpret_cast<int32_t*>(take(4 * nn));
   B->new_e = reinterpret_cast<int64_t*>(take(8 * nn));
-  B->new_row = reinterpret_cast<int64_t*>(take(8 * nn));
+  B->new_d = reinterpret_cast<int64_t*>(take(8 * nn));
   B->size = reinterpret_cast<int32_t*>(take(4 * nn));
   B->cnt = reinterpret_cast<int32_t*>(take(4 * ((size_t)max_deg + 2 + kHist)));
   B->blk_flag = reinterpret_cast<uint8_t*>(take(nn));
@@ -818,6 +889,7 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   B->pull = reinterpret_cast<int32_t*>(take(4 * nn));
   B->b_j = reinterpret_cast<int32_t*>(take(4 * nn));
   B->b_e = reinterpret_cast<int64_t*>(take(8 * nn));
+  B->b_d = reinterpret_cast<int64_t*>(take(8 * nn));
   B->blk_a = reinterpret_cast<int64_t*>(take(8 * ((size_t)grid + 1)));
   B->blk_b = reinterpret_cast<int64_t*>(take(8 * ((size_t)grid + 1)));
 }
@@ -825,7 +897,8 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
 int rounds_grid_size(int device) {
   int sms = 0, per = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rounds, kThreads, 0);
+  cudaFuncSetAttribute(k_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rounds, kThreads, sizeof(Shared));
   if (per < 1) per = 1;
   if (per > 2) per = 2;
   return sms * per;
@@ -840,7 +913,10 @@ cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, int 
   if (b.n <= 0) return cudaSuccess;
   RoundBuffers arg = b;
   void* args[] = {&arg};
-  return cudaLaunchCooperativeKernel((const void*)k_rounds, dim3(grid), dim3(kThreads), args, 0, stream);
+  e = cudaFuncSetAttribute(k_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared));
+  if (e != cudaSuccess) return e;
+  return cudaLaunchCooperativeKernel((const void*)k_rounds, dim3(grid), dim3(kThreads), args, sizeof(Shared),
+                                     stream);
 }
 
 cudaError_t launch_finalize_labels(const RoundBuffers& b, int32_t* labels_out, cudaStream_t stream) {

@@ -82,6 +82,8 @@ def load(build_if_missing: bool = True):
         lib.cc_graph_set_timing.argtypes = [vp, ci]
         lib.cc_last_timings.restype = ci
         lib.cc_last_timings.argtypes = [vp, vp]
+        lib.cc_last_phase_times.restype = ci
+        lib.cc_last_phase_times.argtypes = [vp, vp, i32]
         lib.cc_batch_run.restype = ci
         lib.cc_batch_run.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp, vp, vp]
         _lib = lib
@@ -203,6 +205,15 @@ class Graph:
         ms = (ctypes.c_float * 3)()
         _check("cc_last_timings", self._lib.cc_last_timings(self._h, ctypes.cast(ms, ctypes.c_void_p)))
         return tuple(float(x) for x in ms)
+
+    PHASES = ("rebuild_count", "rebuild_compact", "select_count", "select_emit", "centers_attach",
+              "c4_fixpoint", "removal_decrement")
+
+    def last_phase_times(self):
+        """Milliseconds per phase of the last clustering's round kernel."""
+        ms = (ctypes.c_double * 7)()
+        _check("cc_last_phase_times", self._lib.cc_last_phase_times(self._h, ctypes.cast(ms, ctypes.c_void_p), 7))
+        return dict(zip(self.PHASES, (float(x) for x in ms)))
 
     def disagreements(self, labels) -> int:
         if isinstance(labels, np.ndarray):
