@@ -315,7 +315,10 @@ __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems
       const int last = ws->mark[kLbsW - 1];
       f(L);
       __syncwarp();
+      // next batch: the item holding its first edge is the last item of this
+      // batch or, when an item starts exactly at the next base, its successor
       j0 += last;
+      if (j0 + 1 < nitems && ldcg(epos + j0 + 1) <= base + kLbsW) ++j0;
     }
   }
 }

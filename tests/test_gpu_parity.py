@@ -42,6 +42,13 @@ def small_graphs(gg, seed):
     k = 60
     iu, ju = np.triu_indices(k, 1)
     out.append(gg.from_edges(k, iu.astype(np.int32), ju.astype(np.int32)))   # clique
+    # rows of length one everywhere (a perfect matching) and many small stars:
+    # list items that end exactly on the edge-walker's batch boundaries
+    m = np.arange(0, 5000, 2, dtype=np.int32)
+    out.append(gg.from_edges(5000, m, m + 1))
+    hubs = np.repeat(np.arange(0, 6000, 7, dtype=np.int32), 6)
+    leaves = (hubs + np.tile(np.arange(1, 7, dtype=np.int32), hubs.size // 6)).astype(np.int32)
+    out.append(gg.from_edges(6006, hubs, leaves))
     return out
 
 
