@@ -23,44 +23,41 @@ struct RoundStat {
   int64_t n_alive, delta, k, centers, removed, blocked, edges;
 };
 
-struct GridBarrierHost { unsigned count, gen; };
+// Plan of the next phase, published by the coordinator block at every grid
+// barrier (128 bytes, copied by every block with one vector load).
+struct Plan {
+  int64_t k, need, win_lo, win_len;
+  int64_t take, act_n, act_E, new_n;
+  int64_t new_E, b_n, b_E, undecided;
+  int32_t th, r0, al_sel, al_ident;
+  int32_t state, pad0, pad1, pad2;
+};
+static_assert(sizeof(Plan) == 128, "plan layout");
 
 // Device control block of one clustering job.  Zeroed by the host before
-// each launch; fields are written by the kernels only.
+// each launch; written by the kernels only.
 struct Ctl {
-  GridBarrierHost bar;
+  unsigned arrive, gen;           // grid barrier (monotonic counters)
   int err;
   int algo;
   int64_t eps_ppm;
-  int64_t n, nnz;
-  int32_t max_deg;
-  // state carried across rounds
-  int64_t n_alive;
-  int64_t cursor, al_len;
-  int al_identity, al_sel;
-  int32_t th, top, delta;
-  int64_t k;
-  int need_rebuild, done;
-  int rebuilds_in_row;
-  int64_t round;
-  // active-set selection
-  int64_t need, win_lo, win_len, take, cursor_next;
-  int32_t r0;
-  // per-round lists (counters pack items << 33 | edges)
+  alignas(16) Plan plan;
+  // per-round counters, written by every block (lists pack items << 33 | edges)
   unsigned long long act_pack, new_pack, blk_pack;
-  int64_t act_n, act_E, new_n, new_E, b_n, b_E;
-  int64_t undecided, fix_iter;
-  // per-round tallies
   long long r_centers, r_attached, r_noncenter, r_blocked;
-  long long r_edges;
-  // time per phase category (ns, booked by barrier leaders): rebuild-count,
-  // rebuild-compact, select-count, select-emit, centers+attach, C4 fixpoint
-  // and blocked actives, removal+decrement
-  unsigned long long ph_ns[8];
-  unsigned long long ph_t0;
+  long long undecided;
+  int32_t r0;
+  int64_t cursor_next;
   // objective tallies: member-center edges, member-member edges (counted from
   // both ends), sum over clusters of C(size, 2)
   unsigned long long mc, mm, pairs;
+  // results, written by the coordinator at the end
+  int64_t round, n_alive;
+  int done;
+  // time per phase category (ns): rebuild-count, rebuild-compact,
+  // select-count, select-emit, centers+attach, C4 fixpoint and blocked
+  // actives, removal+decrement, setup
+  unsigned long long ph_ns[8];
 };
 
 struct RoundBuffers {
@@ -70,8 +67,8 @@ struct RoundBuffers {
   const int32_t* col;
   const int32_t* order;
   unsigned long long* st;      // per-vertex state word
-  int32_t* al0;
-  int32_t* al1;
+  int2* al0;                   // alive lists: (rank, vertex), rank-ordered
+  int2* al1;
   // row lists (see RowList in cc_device.cuh): vertex, first virtual edge,
   // CSR delta; actives also keep their rank, the blocked list stores the
   // active-list index in place of a vertex

@@ -1,10 +1,12 @@
 // cc_rounds.cu -- the bulk-synchronous rounds of C4 and ClusterWild! (Alg. 2)
 // as one persistent cooperative kernel.
 //
-// All rounds run inside a single launch; the barrier at the end of each
-// phase is a grid barrier (bounded wait), and the last block to reach a
-// barrier does that barrier's serial bookkeeping (the Delta walk, batch size,
-// statistics) before releasing the others.  The host is not involved between
+// All rounds run inside a single launch.  Phases are separated by grid
+// barriers; block 0 is the coordinator: at every barrier it waits for all
+// blocks, does the serial bookkeeping of the round (Delta walk, batch size,
+// selection windows, statistics) on state it keeps in its own shared memory,
+// publishes a 128-byte plan and releases the others, which copy the plan with
+// one vector load.  Every wait is bounded.  The host is not involved between
 // rounds.
 //
 // Per-vertex state: one 64-bit word st[v] = (hi:int32, lo:uint32)
@@ -41,9 +43,11 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kHist = 2048;                  // shared-memory window of the degree table
+constexpr int kScanU = 4;                    // alive-list entries per thread per scan step
 constexpr int32_t kAliveHi = 0x7FFFFFFF;
 constexpr uint32_t kUndecided = 0, kCenter = 1, kNonCenter = 2;
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
+constexpr int kRun = 0, kDone = 1, kRebuild = 2, kAbort = 3;
 
 __device__ __forceinline__ int32_t hi_of(unsigned long long x) { return (int32_t)(x >> 32); }
 __device__ __forceinline__ uint32_t lo_of(unsigned long long x) { return (uint32_t)x; }
@@ -55,12 +59,28 @@ __device__ __forceinline__ unsigned long long word(int32_t hi, uint32_t lo) {
 template <class T>
 __device__ __forceinline__ T vload(const T* p) { return *reinterpret_cast<const volatile T*>(p); }
 
+__device__ __forceinline__ void atom_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Coordinator state, in block 0's shared memory for the whole kernel.
+struct Coord {
+  int64_t n, n_alive, cursor, al_len, k, round, stats_cap, eps_ppm;
+  int64_t need, win_lo, win_len, r_edges, fix_iter;
+  int32_t th, top, delta, max_deg;
+  int algo, al_sel, al_ident, rebuilds_in_row;
+  unsigned long long t0;
+  unsigned long long ph_ns[8];
+};
+
 // Shared memory of one block (dynamic: larger than the 48 KB static limit).
 struct Shared {
-  unsigned gen;
-  int leader, ok;
+  Plan plan;
+  Coord co;
+  int ok;
+  int dec;
   int64_t scr[33];
-  int64_t bcast[2];
+  int64_t bcast[8];
   int32_t hist[kHist];
   LbsWarp lbs[kWarps];
   AppendBuf app[kWarps];
@@ -78,10 +98,75 @@ struct K {
   Ctl* C;
   Shared* S;
   unsigned G;
+  unsigned epoch;
   Tally t;
 
-  // plain control-block fields, always accessed at L2
-  __device__ __forceinline__ volatile Ctl* vc() const { return C; }
+  __device__ __forceinline__ const Plan& P() const { return S->plan; }
+  __device__ __forceinline__ Coord& co() const { return S->co; }
+  __device__ void fail(int code) { atomicCAS(&C->err, kOk, code); }
+
+  // ---------------- grid barrier with the coordinator -------------------------
+  // All blocks call sync(); block 0 waits for every arrival, books the time
+  // since the previous barrier to phase `cat`, runs act() with its whole
+  // block (writing S->plan), publishes the plan and releases.  The others
+  // wait for the release and copy the plan.  Returns false once the run
+  // must stop (error, or the plan says so).
+  template <class A>
+  __device__ bool sync(int cat, A&& act) {
+    __syncthreads();
+    ++epoch;
+    if (threadIdx.x == 0) atom_add_release(&C->arrive, 1u);
+    if (blockIdx.x == 0) {
+      if (threadIdx.x == 0) {
+        const unsigned target = G * epoch;
+        const uint64_t t0 = globaltimer_ns();
+        unsigned spins = 0;
+        int ok = 1;
+        while (ld_acquire(&C->arrive) < target) {
+          if ((++spins & 63) == 0) {
+            if (ld_volatile_int(&C->err) != kOk) { ok = 0; break; }
+            if (globaltimer_ns() - t0 > kBarrierLimitNs) { atomicCAS(&C->err, kOk, kErrTimeout); ok = 0; break; }
+          }
+        }
+        if (ld_volatile_int(&C->err) != kOk) ok = 0;
+        const unsigned long long now = globaltimer_ns();
+        S->co.ph_ns[cat] += now - S->co.t0;
+        S->co.t0 = now;
+        S->ok = ok;
+      }
+      __syncthreads();
+      if (S->ok) act();
+      __syncthreads();
+      if (threadIdx.x == 0 && (!S->ok || ld_volatile_int(&C->err) != kOk)) S->plan.state = kAbort;
+      __syncthreads();
+      // publish: 128 bytes as eight 16-byte stores, then release
+      if (threadIdx.x < sizeof(Plan) / 16)
+        reinterpret_cast<int4*>(&C->plan)[threadIdx.x] = reinterpret_cast<const int4*>(&S->plan)[threadIdx.x];
+      __syncthreads();
+      if (threadIdx.x == 0) st_release(&C->gen, epoch);
+    } else {
+      if (threadIdx.x == 0) {
+        const uint64_t t0 = globaltimer_ns();
+        unsigned spins = 0;
+        while (ld_acquire(&C->gen) < epoch) {
+          if ((++spins & 63) == 0) {
+            if (ld_volatile_int(&C->err) != kOk) break;
+            if (globaltimer_ns() - t0 > kBarrierLimitNs) { atomicCAS(&C->err, kOk, kErrTimeout); break; }
+          }
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x < sizeof(Plan) / 16)
+        reinterpret_cast<int4*>(&S->plan)[threadIdx.x] = __ldcg(reinterpret_cast<const int4*>(&C->plan) + threadIdx.x);
+      __syncthreads();
+      if (threadIdx.x == 0 && ld_volatile_int(&C->err) != kOk) S->plan.state = kAbort;
+      __syncthreads();
+    }
+    return S->plan.state != kAbort;
+  }
+  __device__ bool sync(int cat) {
+    return sync(cat, [] {});
+  }
 
   // ---------------- degree-count table --------------------------------------
   __device__ void hist_add(int32_t th, uint32_t d, int delta) {
@@ -102,23 +187,6 @@ struct K {
     __syncthreads();
   }
 
-  // ---------------- barrier --------------------------------------------------
-  // Arrive at a grid barrier; the leader books the time since the previous
-  // barrier to phase category `cat` (a cheap always-on profile of the rounds).
-  __device__ bool arrive(int cat) {
-    const bool lead = bar_arrive(reinterpret_cast<GridBarrier*>(&C->bar), G, &S->gen, &S->leader);
-    if (lead && threadIdx.x == 0) {
-      const unsigned long long now = globaltimer_ns();
-      vc()->ph_ns[cat] += now - vc()->ph_t0;
-      vc()->ph_t0 = now;
-    }
-    return lead;
-  }
-  __device__ bool finish(bool lead) {
-    return bar_finish(reinterpret_cast<GridBarrier*>(&C->bar), lead, &S->gen, &C->err, &S->ok);
-  }
-  __device__ void fail(int code) { atomicCAS(&C->err, kOk, code); }
-
   __device__ RowList new_list() const { return RowList{B.new_v, B.new_e, B.new_d, nullptr, &C->new_pack}; }
   __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, nullptr, &C->blk_pack}; }
   __device__ LbsWarp* lbs_ws() const { return &S->lbs[threadIdx.x >> 5]; }
@@ -138,8 +206,10 @@ struct K {
     if (want) t.pairs += 1ull + (unsigned long long)(old + __popc(grp & ((1u << lane) - 1u)));
   }
 
-  __device__ int32_t al_at(int sel, int identity, int64_t i) const {
-    if (identity) return (int32_t)i;
+  // Entry i of the current alive list: (rank, vertex).  Before the first
+  // compaction the list is implicit: entry i is (i, order[i]).
+  __device__ int2 al_at(int sel, int identity, int64_t i) const {
+    if (identity) return make_int2((int32_t)i, __ldg(B.order + i));
     return ldcg((sel ? B.al1 : B.al0) + i);
   }
 
@@ -151,8 +221,8 @@ struct K {
     if (*s > *e) *s = *e;
   }
 
-  // Exclusive prefix of blk_a[0..G) in place; returns the total.  Leader only.
-  __device__ int64_t leader_prefix_blocks() {
+  // Coordinator: exclusive prefix of blk_a[0..G) in place; returns the total.
+  __device__ int64_t prefix_blocks() {
     int64_t run = 0;
     for (unsigned base = 0; base < G; base += blockDim.x) {
       const unsigned b = base + threadIdx.x;
@@ -166,7 +236,7 @@ struct K {
     return run;
   }
 
-  __device__ int64_t leader_max_blocks() {
+  __device__ int64_t max_blocks() {
     int64_t m = 0;
     for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
       const int64_t x = ldcg(B.blk_b + b);
@@ -175,71 +245,141 @@ struct K {
     return block_max<int64_t>(m, S->scr);
   }
 
-  // ---------------- round planning (leader) ----------------------------------
-  // Sets Delta, k and the first selection window, or asks for a rebuild.
-  __device__ void plan_round() {
-    __shared__ int s_dec;
+  // ---------------- coordinator actions ----------------------------------------
+  __device__ void co_init() {
     if (threadIdx.x == 0) {
-      const int64_t n_alive = vc()->n_alive;
-      int dec = 0;
-      if (n_alive <= 0) { vc()->done = 1; dec = 1; }
-      else if (!vc()->al_identity && vc()->al_len - vc()->cursor > 4 * n_alive + 65536) { vc()->need_rebuild = 1; dec = 1; }
-      s_dec = dec;
+      Coord& c = co();
+      c.n = B.n;
+      c.n_alive = B.n;
+      c.cursor = 0;
+      c.al_len = B.n;
+      c.al_ident = 1;
+      c.al_sel = 0;
+      c.max_deg = B.max_deg;
+      c.th = B.max_deg + 1;       // nothing tracked: the first rebuild fills the table
+      c.top = B.max_deg;
+      c.round = 0;
+      c.rebuilds_in_row = 0;
+      c.algo = vload(&C->algo);
+      c.eps_ppm = vload(&C->eps_ppm);
+      c.stats_cap = B.stats_cap;
+      Plan& p = S->plan;
+      p = Plan{};
+      p.state = B.n > 0 ? kRebuild : kDone;
+      p.r0 = -1;
     }
     __syncthreads();
-    if (s_dec) return;
-    // walk the degree table down from `top`
-    const int32_t th = vc()->th;
-    int32_t t = vc()->top;
+    rebuild_plan_fields();
+  }
+
+  // Sets Delta, k and the first selection window, or asks for a rebuild.
+  __device__ void plan_round() {
+    Coord& c = co();
+    Plan& p = S->plan;
+    if (threadIdx.x == 0) {
+      int dec = 0;
+      if (c.n_alive <= 0) { p.state = kDone; dec = 1; }
+      else if (!c.al_ident && c.al_len - c.cursor > 4 * c.n_alive + 65536) { p.state = kRebuild; dec = 1; }
+      S->dec = dec;
+    }
+    __syncthreads();
+    if (S->dec) return;
+    // walk the degree table down from `top`, four bins per thread per step
+    const int32_t th = c.th;
+    int32_t tt = c.top;
     int32_t found = -1;
-    while (t >= th) {
-      // four bins per thread per step: t, t-1, ... t-4*blockDim+1
+    while (tt >= th) {
       int32_t hit = -1;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int32_t d = t - (int32_t)(threadIdx.x * 4 + q);
+        const int32_t d = tt - (int32_t)(threadIdx.x * 4 + q);
         if (d >= th && hit < 0 && ldcg(B.cnt + d) > 0) hit = d;
       }
       found = (int32_t)block_max<int64_t>(hit, S->scr);
       if (found >= 0) break;
-      t -= 4 * (int32_t)blockDim.x;
+      tt -= 4 * (int32_t)blockDim.x;
     }
     if (threadIdx.x == 0) {
-      int32_t delta;
-      if (found >= 0) { delta = found; vc()->top = found; }
-      else if (th <= 1) { delta = 0; vc()->top = 0; }
-      else { vc()->need_rebuild = 1; s_dec = 1; }
-      if (!s_dec) {
-        const int64_t n_alive = vc()->n_alive;
+      int32_t delta = 0;
+      bool ok = true;
+      if (found >= 0) { delta = found; c.top = found; }
+      else if (th <= 1) { delta = 0; c.top = 0; }
+      else { p.state = kRebuild; ok = false; }
+      if (ok) {
         int64_t k;
-        if (delta <= 0) k = n_alive;
+        if (delta <= 0) k = c.n_alive;
         else {
-          const unsigned long long num = (unsigned long long)vc()->eps_ppm * (unsigned long long)n_alive;
+          const unsigned long long num = (unsigned long long)c.eps_ppm * (unsigned long long)c.n_alive;
           const unsigned long long den = 1000000ull * (unsigned long long)delta;
           k = (int64_t)((num + den - 1) / den);
           if (k < 1) k = 1;
-          if (k > n_alive) k = n_alive;
+          if (k > c.n_alive) k = c.n_alive;
         }
-        vc()->delta = delta;
-        vc()->k = k;
-        vc()->need = k;
-        vc()->win_lo = vc()->cursor;
-        const int64_t avail = vc()->al_len - vc()->cursor;
-        const int64_t est = (int64_t)((double)k * (double)avail / (double)n_alive * 1.05) + 256;
-        vc()->win_len = est < avail ? est : avail;
-        vc()->act_pack = 0; vc()->new_pack = 0; vc()->blk_pack = 0;
-        vc()->r_centers = 0; vc()->r_attached = 0; vc()->r_noncenter = 0; vc()->r_blocked = 0; vc()->r_edges = 0;
-        vc()->r0 = -1;
+        c.delta = delta;
+        c.k = k;
+        c.need = k;
+        c.win_lo = c.cursor;
+        const int64_t avail = c.al_len - c.cursor;
+        const int64_t est = (int64_t)((double)k * (double)avail / (double)c.n_alive * 1.05) + 256;
+        c.win_len = est < avail ? est : avail;
+        c.r_edges = 0;
+        // counters of the round
+        C->act_pack = 0; C->new_pack = 0; C->blk_pack = 0;
+        C->r_centers = 0; C->r_attached = 0; C->r_noncenter = 0; C->r_blocked = 0;
+        C->r0 = -1;
+        p.state = kRun;
+        p.k = k;
+        p.need = k;
+        p.win_lo = c.win_lo;
+        p.win_len = c.win_len;
+        p.th = c.th;
+        p.r0 = -1;
+        p.al_sel = c.al_sel;
+        p.al_ident = c.al_ident;
       }
     }
     __syncthreads();
   }
 
+  // Statistics and n_i update after the removal phase, then the next plan.
+  __device__ void co_end_round() {
+    Coord& c = co();
+    if (threadIdx.x < 6) {
+      const long long* src[6] = {&C->r_centers, &C->r_attached, &C->r_noncenter, &C->r_blocked,
+                                 reinterpret_cast<const long long*>(&C->new_pack), nullptr};
+      if (threadIdx.x < 5) S->bcast[threadIdx.x] = vload(src[threadIdx.x]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int64_t centers_seen = S->bcast[0], attached = S->bcast[1], noncenter = S->bcast[2];
+      const int64_t blocked = S->bcast[3];
+      const unsigned long long np = (unsigned long long)S->bcast[4];
+      const int64_t k = c.k;
+      const int64_t removed = k + attached;
+      const int64_t centers = k - noncenter;
+      const int64_t r = c.round;
+      if (r < c.stats_cap) {
+        RoundStat s;
+        s.n_alive = c.n_alive; s.delta = c.delta; s.k = k; s.centers = centers;
+        s.removed = removed; s.blocked = blocked; s.edges = c.r_edges + (int64_t)(np & kPackEdgeMask);
+        B.stats[r] = s;
+      }
+      if (centers_seen != centers) fail(kErrInternal);
+      c.n_alive -= removed;
+      if (c.n_alive < 0) fail(kErrInternal);
+      c.round = r + 1;
+      c.rebuilds_in_row = 0;
+      if (c.round > c.n + 1) fail(kErrInternal);
+    }
+    __syncthreads();
+    plan_round();
+  }
+
   // ---------------- rebuild: compact the alive list, refill the table -------
   __device__ bool rebuild() {
-    const int sel = vload(&C->al_sel), ident = vload(&C->al_identity);
-    const int64_t lo = vload(&C->cursor), len = vload(&C->al_len) - lo;
-    const int32_t top = vload(&C->top);
+    const int sel = P().al_sel, ident = P().al_ident;
+    const int64_t lo = P().win_lo, len = P().win_len;     // the live part of the list
+    const int32_t top = P().th;                            // zero bins [0, top + 1 + kHist)
     // A: zero the table, count alive and find the largest degree per block
     const int64_t zhi = (int64_t)top + 1 + kHist;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < zhi && i <= (int64_t)B.max_deg + 1 + kHist;
@@ -248,96 +388,132 @@ struct K {
     int64_t s, e;
     slice(lo, len, &s, &e);
     int64_t cnt = 0, mx = 0;
-    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-      const int32_t r = al_at(sel, ident, i);
-      const unsigned long long x = ldcg(B.st + __ldg(B.order + r));
-      if (hi_of(x) == kAliveHi) { ++cnt; mx = lo_of(x) > mx ? lo_of(x) : mx; }
+    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+      int2 a[kScanU];
+      unsigned long long x[kScanU];
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+        a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) x[q] = a[q].y >= 0 ? ldcg(B.st + a[q].y) : 0;
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q)
+        if (a[q].y >= 0 && hi_of(x[q]) == kAliveHi) { ++cnt; mx = lo_of(x[q]) > mx ? lo_of(x[q]) : mx; }
     }
     cnt = block_sum<int64_t>(cnt, S->scr);
     mx = block_max<int64_t>(mx, S->scr);
     if (threadIdx.x == 0) { B.blk_a[blockIdx.x] = cnt; B.blk_b[blockIdx.x] = mx; }
-    bool lead = arrive(0);
-    if (lead) {
-      const int64_t tot = leader_prefix_blocks();
-      const int64_t D = leader_max_blocks();
-      if (threadIdx.x == 0) {
-        if (tot != vc()->n_alive) fail(kErrInternal);
-        vc()->take = tot;                 // new list length
-        vc()->top = (int32_t)D;
-        const int32_t th = (int32_t)(D >> 2);
-        vc()->th = th < 1 ? 1 : th;
-      }
-    }
-    if (!finish(lead)) return false;
+    if (!sync(0, [&] {
+          const int64_t tot = prefix_blocks();
+          const int64_t D = max_blocks();
+          if (threadIdx.x == 0) {
+            Coord& c = co();
+            if (tot != c.n_alive) fail(kErrInternal);
+            c.top = (int32_t)D;
+            const int32_t th = (int32_t)(D >> 2);
+            c.th = th < 1 ? 1 : th;
+            S->plan.th = c.th;
+            S->plan.take = tot;
+          }
+        }))
+      return false;
     // B: stable compaction into the other buffer, refill the table
-    const int32_t th = vload(&C->th);
-    int32_t* dst = sel ? B.al0 : B.al1;
+    const int32_t th = P().th;
+    int2* dst = sel ? B.al0 : B.al1;
     int64_t run = ldcg(B.blk_a + blockIdx.x);
-    for (int64_t base = s; base < e; base += blockDim.x) {
-      const int64_t i = base + threadIdx.x;
-      int32_t r = 0;
-      uint32_t d = 0;
-      int64_t alive = 0;
-      if (i < e) {
-        r = al_at(sel, ident, i);
-        const unsigned long long x = ldcg(B.st + __ldg(B.order + r));
-        if (hi_of(x) == kAliveHi) { alive = 1; d = lo_of(x); }
+    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+      int2 a[kScanU];
+      unsigned long long x[kScanU];
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+        a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
       }
+      int64_t mine = 0;
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) x[q] = a[q].y >= 0 ? ldcg(B.st + a[q].y) : 0;
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) mine += (a[q].y >= 0 && hi_of(x[q]) == kAliveHi) ? 1 : 0;
       int64_t tot;
-      const int64_t ex = block_exclusive_sum<int64_t>(alive, S->scr, &tot);
-      if (alive) {
-        dst[run + ex] = r;
-        hist_add(th, d, 1);
+      int64_t o = run + block_exclusive_sum<int64_t>(mine, S->scr, &tot);
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        if (a[q].y >= 0 && hi_of(x[q]) == kAliveHi) {
+          dst[o++] = a[q];
+          hist_add(th, lo_of(x[q]), 1);
+        }
       }
       run += tot;
     }
     hist_flush(th);
-    lead = arrive(1);
-    if (lead) {
+    return sync(1, [&] {
       if (threadIdx.x == 0) {
-        vc()->al_sel = sel ^ 1;
-        vc()->al_identity = 0;
-        vc()->al_len = vc()->take;
-        vc()->cursor = 0;
-        vc()->need_rebuild = 0;
+        Coord& c = co();
+        c.al_sel = sel ^ 1;
+        c.al_ident = 0;
+        c.al_len = S->plan.take;
+        c.cursor = 0;
         // a rebuild always leaves a tracked vertex (or Delta = 0), so two in a
         // row without a round in between mean the table is inconsistent
-        vc()->rebuilds_in_row += 1;
-        if (vc()->rebuilds_in_row > 2) fail(kErrInternal);
+        c.rebuilds_in_row += 1;
+        if (c.rebuilds_in_row > 2) fail(kErrInternal);
       }
       __syncthreads();
       plan_round();
+      rebuild_plan_fields();
+    });
+  }
+
+  // When the plan asks for a rebuild, it carries the live part of the alive
+  // list and the zeroing bound in (win_lo, win_len, th).
+  __device__ void rebuild_plan_fields() {
+    if (threadIdx.x == 0 && S->plan.state == kRebuild) {
+      Coord& c = co();
+      S->plan.al_sel = c.al_sel;
+      S->plan.al_ident = c.al_ident;
+      S->plan.win_lo = c.cursor;
+      S->plan.win_len = c.al_len - c.cursor;
+      S->plan.th = c.top;
     }
-    return finish(lead);
+    __syncthreads();
   }
 
   // ---------------- active-set selection (Alg. 2: A = next k alive of pi) ----
-  // Called by every thread of the block for one tile of the window; threads
-  // with want == true hold an active vertex v of rank r.
-  __device__ void emit_actives(int32_t v, int32_t r, int algo, int32_t th, bool want) {
-    uint32_t d = 0;
-    int64_t deg0 = 0, row = 0;
-    int64_t listed = 0;
-    if (want) {
-      const unsigned long long x = ldcg(B.st + v);
-      d = lo_of(x);
+  // Called by every thread of the block for one tile of the window; entry q
+  // of a thread is an active vertex (rank a[q].x, vertex a[q].y) when want[q].
+  __device__ void emit_actives(const int2* a, const bool* want, int algo, int32_t th) {
+    int64_t deg0[kScanU], row[kScanU];
+    bool listed[kScanU];
+    int64_t nl = 0, el = 0;
+#pragma unroll
+    for (int q = 0; q < kScanU; ++q) {
+      listed[q] = false;
+      deg0[q] = 0;
+      row[q] = 0;
+      if (!want[q]) continue;
+      const int32_t r = a[q].x, v = a[q].y;
+      const uint32_t d = lo_of(ldcg(B.st + v));
       hist_add(th, d, -1);                      // v leaves the graph this round
       B.size[r] = 0;
       if (d == 0) {                             // no alive neighbour: singleton center
         B.st[v] = word(r, 0);
         t.centers += 1;
       } else {
-        row = __ldg(B.off + v);
-        deg0 = __ldg(B.off + v + 1) - row;
+        row[q] = __ldg(B.off + v);
+        deg0[q] = __ldg(B.off + v + 1) - row[q];
         B.st[v] = word(~r, algo == kAlgoCW ? kCenter : kUndecided);
-        listed = 1;
+        listed[q] = true;
+        nl += 1;
+        el += deg0[q];
         if (algo == kAlgoCW) t.centers += 1;
       }
     }
     // one atomic per block and tile on the packed list counter
     int64_t cnt_tot, e_tot;
-    const int64_t jx = block_exclusive_sum<int64_t>(listed, S->scr, &cnt_tot);
-    const int64_t ex = block_exclusive_sum<int64_t>(listed ? deg0 : 0, S->scr, &e_tot);
+    const int64_t jx = block_exclusive_sum<int64_t>(nl, S->scr, &cnt_tot);
+    const int64_t ex = block_exclusive_sum<int64_t>(el, S->scr, &e_tot);
     if (cnt_tot == 0) return;
     if (threadIdx.x == 0) {
       const unsigned long long old =
@@ -346,92 +522,129 @@ struct K {
       S->bcast[1] = (int64_t)(old & kPackEdgeMask);
     }
     __syncthreads();
-    const int64_t j = S->bcast[0] + jx, ep = S->bcast[1] + ex;
+    int64_t j = S->bcast[0] + jx, ep = S->bcast[1] + ex;
     __syncthreads();
-    if (listed) {
-      B.act_v[j] = v;
-      B.act_r[j] = r;
+#pragma unroll
+    for (int q = 0; q < kScanU; ++q) {
+      if (!listed[q]) continue;
+      B.act_v[j] = a[q].y;
+      B.act_r[j] = a[q].x;
       B.act_e[j] = ep;
-      B.act_d[j] = row - ep;
+      B.act_d[j] = row[q] - ep;
       B.blk_flag[j] = 0;
+      ++j;
+      ep += deg0[q];
     }
   }
 
   __device__ bool select(int algo) {
     for (;;) {
-      const int sel = vload(&C->al_sel), ident = vload(&C->al_identity);
-      const int64_t wlo = vload(&C->win_lo), wlen = vload(&C->win_len);
+      const int sel = P().al_sel, ident = P().al_ident;
+      const int64_t wlo = P().win_lo, wlen = P().win_len;
       int64_t s, e;
       slice(wlo, wlen, &s, &e);
       // S1: alive count per block
       int64_t cnt = 0;
-      for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) {
-        const int32_t r = al_at(sel, ident, i);
-        if (hi_of(ldcg(B.st + __ldg(B.order + r))) == kAliveHi) ++cnt;
+      for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+        int2 a[kScanU];
+#pragma unroll
+        for (int q = 0; q < kScanU; ++q) {
+          const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+          a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
+        }
+#pragma unroll
+        for (int q = 0; q < kScanU; ++q)
+          cnt += (a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi) ? 1 : 0;
       }
       cnt = block_sum<int64_t>(cnt, S->scr);
       if (threadIdx.x == 0) B.blk_a[blockIdx.x] = cnt;
-      bool lead = arrive(2);
-      if (lead) {
-        const int64_t tot = leader_prefix_blocks();
-        if (threadIdx.x == 0) {
-          const int64_t need = vc()->need;
-          vc()->take = tot < need ? tot : need;
-        }
-      }
-      if (!finish(lead)) return false;
+      if (!sync(2, [&] {
+            const int64_t tot = prefix_blocks();
+            if (threadIdx.x == 0) {
+              const int64_t need = co().need;
+              S->plan.take = tot < need ? tot : need;
+            }
+          }))
+        return false;
       // S2: emit the first `take` alive entries of the window
-      const int64_t take = vload(&C->take), need = vload(&C->need);
-      const bool first_window = vload(&C->r0) < 0;
-      const int32_t th = vload(&C->th);
+      const int64_t take = P().take, need = P().need;
+      const bool first_window = P().r0 < 0;
+      const int32_t th = P().th;
       int64_t run = ldcg(B.blk_a + blockIdx.x);
       if (run < take) {
-        for (int64_t base = s; base < e; base += blockDim.x) {
-          const int64_t i = base + threadIdx.x;
-          int32_t r = 0, v = 0;
-          int64_t alive = 0;
-          if (i < e) {
-            r = al_at(sel, ident, i);
-            v = __ldg(B.order + r);
-            alive = hi_of(ldcg(B.st + v)) == kAliveHi ? 1 : 0;
+        for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+          int2 a[kScanU];
+          bool alive[kScanU];
+          int64_t mine = 0;
+#pragma unroll
+          for (int q = 0; q < kScanU; ++q) {
+            const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+            a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
+          }
+#pragma unroll
+          for (int q = 0; q < kScanU; ++q) {
+            alive[q] = a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi;
+            mine += alive[q] ? 1 : 0;
           }
           int64_t tot;
-          const int64_t g = run + block_exclusive_sum<int64_t>(alive, S->scr, &tot);
-          const bool want = alive && g < take;
-          if (want && g == 0 && first_window) vc()->r0 = r;
-          if (want && take == need && g == take - 1) vc()->cursor_next = i + 1;
-          emit_actives(v, r, algo, th, want);
+          int64_t g = run + block_exclusive_sum<int64_t>(mine, S->scr, &tot);
+          bool want[kScanU];
+#pragma unroll
+          for (int q = 0; q < kScanU; ++q) {
+            want[q] = alive[q] && g < take;
+            if (want[q] && g == 0 && first_window) C->r0 = a[q].x;
+            if (want[q] && take == need && g == take - 1)
+              C->cursor_next = base + (int64_t)threadIdx.x * kScanU + q + 1;
+            g += alive[q] ? 1 : 0;
+          }
+          emit_actives(a, want, algo, th);
           run += tot;
           if (run >= take) break;           // uniform across the block
         }
       }
       hist_flush(th);
-      lead = arrive(3);
-      if (lead && threadIdx.x == 0) {
-        const int64_t left = vc()->need - vc()->take;
-        vc()->need = left;
-        if (left == 0) {
-          vc()->cursor = vc()->cursor_next;
-          const unsigned long long p = vc()->act_pack;
-          vc()->act_n = (int64_t)(p >> kPackShift);
-          vc()->act_E = (int64_t)(p & kPackEdgeMask);
-          // adjacency passes over the active rows: attach (and C4 detection)
-          vc()->r_edges = vc()->act_E * (vc()->algo == kAlgoC4 ? 2 : 1);
-        } else {
-          const int64_t lo2 = vc()->win_lo + vc()->win_len;
-          const int64_t avail = vc()->al_len - lo2;
-          const int64_t alive_left = vc()->n_alive - (vc()->k - left);
-          if (avail <= 0 || alive_left <= 0) {
-            fail(kErrInternal);
-          } else {
-            const int64_t est = (int64_t)((double)left * (double)avail / (double)alive_left * 1.1) + 1024;
-            vc()->win_lo = lo2;
-            vc()->win_len = est < avail ? est : avail;
-          }
-        }
-      }
-      if (!finish(lead)) return false;
-      if (vload(&C->need) == 0) return true;
+      if (!sync(3, [&] {
+            if (threadIdx.x == 0) {
+              Coord& c = co();
+              Plan& p = S->plan;
+              if (p.r0 < 0) p.r0 = vload(&C->r0);
+              const int64_t left = c.need - p.take;
+              c.need = left;
+              p.need = left;
+              if (left == 0) {
+                c.cursor = vload(&C->cursor_next);
+                const unsigned long long pk = vload(&C->act_pack);
+                p.act_n = (int64_t)(pk >> kPackShift);
+                p.act_E = (int64_t)(pk & kPackEdgeMask);
+                // adjacency passes over the active rows: attach (and C4 detection)
+                c.r_edges = p.act_E * (c.algo == kAlgoC4 ? 2 : 1);
+              } else {
+                const int64_t lo2 = c.win_lo + c.win_len;
+                const int64_t avail = c.al_len - lo2;
+                const int64_t alive_left = c.n_alive - (c.k - left);
+                if (avail <= 0 || alive_left <= 0) {
+                  fail(kErrInternal);
+                } else {
+                  const int64_t est = (int64_t)((double)left * (double)avail / (double)alive_left * 1.1) + 1024;
+                  c.win_lo = lo2;
+                  c.win_len = est < avail ? est : avail;
+                  p.win_lo = c.win_lo;
+                  p.win_len = c.win_len;
+                }
+              }
+            }
+          }))
+        return false;
+      if (P().need == 0) return true;
+    }
+  }
+
+  // Coordinator: list sizes after the attachment passes.
+  __device__ void co_lists_ready() {
+    if (threadIdx.x == 0) {
+      const unsigned long long pk = vload(&C->new_pack);
+      S->plan.new_n = (int64_t)(pk >> kPackShift);
+      S->plan.new_E = (int64_t)(pk & kPackEdgeMask);
     }
   }
 
@@ -468,7 +681,7 @@ struct K {
   }
 
   __device__ void attach_from_actives(bool skip_blocked, int32_t th) {
-    const int64_t an = vload(&C->act_n), aE = vload(&C->act_E);
+    const int64_t an = P().act_n, aE = P().act_E;
     lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
       bool push[kLbsK];
       int32_t r[kLbsK], u[kLbsK];
@@ -492,8 +705,8 @@ struct K {
 
   // ---------------- C4: blocked detection ------------------------------------
   __device__ void c4_detect() {
-    const int64_t an = vload(&C->act_n), aE = vload(&C->act_E);
-    const int32_t r0 = vload(&C->r0);
+    const int64_t an = P().act_n, aE = P().act_E;
+    const int32_t r0 = P().r0;
     lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
       int32_t rv[kLbsK], u[kLbsK];
       int64_t pos[kLbsK];
@@ -516,7 +729,7 @@ struct K {
 
   // C4: unblocked actives become centers; blocked ones go to the blocked list.
   __device__ void c4_classify() {
-    const int64_t an = vload(&C->act_n);
+    const int64_t an = P().act_n;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)G * blockDim.x) >> 5;
@@ -542,7 +755,7 @@ struct K {
 
   // Reset the per-item scratch of the blocked list (after its counter is known).
   __device__ void c4_blocked_init() {
-    const int64_t bn = vload(&C->b_n);
+    const int64_t bn = P().b_n;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
       B.hit_c[q] = 0;
       B.hit_p[q] = 0;
@@ -553,8 +766,8 @@ struct K {
   // C4 fixpoint, step 1: look at the earlier active neighbours of every
   // undecided blocked vertex.
   __device__ void c4_fix_scan() {
-    const int64_t bn = vload(&C->b_n), bE = vload(&C->b_E);
-    const int32_t r0 = vload(&C->r0);
+    const int64_t bn = P().b_n, bE = P().b_E;
+    const int32_t r0 = P().r0;
     lbs_for_each(B.b_e, bn, bE, lbs_ws(), [&](const Lbs& L) {
 #pragma unroll
       for (int i = 0; i < kLbsK; ++i) {
@@ -576,7 +789,7 @@ struct K {
 
   // C4 fixpoint, step 2: decide (isCenter without waiting).
   __device__ long long c4_fix_decide() {
-    const int64_t bn = vload(&C->b_n);
+    const int64_t bn = P().b_n;
     long long left = 0;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
       const int32_t j = ldcg(B.b_j + q);
@@ -594,8 +807,8 @@ struct K {
   // C4 after the fixpoint: blocked centers push, blocked non-centers pull the
   // lowest center rank among their neighbours.
   __device__ void c4_blocked_attach(int32_t th) {
-    const int64_t bn = vload(&C->b_n), bE = vload(&C->b_E);
-    const int32_t r0 = vload(&C->r0);
+    const int64_t bn = P().b_n, bE = P().b_E;
+    const int32_t r0 = P().r0;
     lbs_for_each(B.b_e, bn, bE, lbs_ws(), [&](const Lbs& L) {
 #pragma unroll
       for (int i = 0; i < kLbsK; ++i) {
@@ -623,7 +836,7 @@ struct K {
 
   // C4: a non-center active takes its pulled label and joins the removal list.
   __device__ void c4_pull_finalize() {
-    const int64_t bn = vload(&C->b_n);
+    const int64_t bn = P().b_n;
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)G * blockDim.x) >> 5;
@@ -650,9 +863,9 @@ struct K {
   }
 
   // ---------------- removal: residual degrees and the objective --------------
+  // ---------------- removal: residual degrees and the objective --------------
   __device__ void decrement(int32_t th) {
-    const unsigned long long p = vload(&C->new_pack);
-    const int64_t nn = (int64_t)(p >> kPackShift), nE = (int64_t)(p & kPackEdgeMask);
+    const int64_t nn = P().new_n, nE = P().new_E;
     lbs_for_each(B.new_e, nn, nE, lbs_ws(), [&](const Lbs& L) {
       int32_t u[kLbsK], w[kLbsK], lu[kLbsK];
       int64_t pos[kLbsK];
@@ -700,110 +913,97 @@ struct K {
     if (threadIdx.x == 0 && pr != 0) atomicAdd(&C->pairs, pr);
     t = Tally{0, 0, 0, 0, 0, 0, 0};
   }
-
-  // Leader at the end of a round: statistics, n_i update, plan the next round.
-  __device__ void end_round() {
-    if (threadIdx.x == 0) {
-      const int64_t k = vc()->k;
-      const int64_t removed = k + vc()->r_attached;
-      const int64_t centers = k - vc()->r_noncenter;
-      const int64_t r = vc()->round;
-      if (r < B.stats_cap) {
-        RoundStat s;
-        s.n_alive = vc()->n_alive; s.delta = vc()->delta; s.k = k; s.centers = centers;
-        s.removed = removed; s.blocked = vc()->r_blocked; s.edges = vc()->r_edges + (int64_t)(vc()->new_pack & kPackEdgeMask);
-        B.stats[r] = s;
-      }
-      if (vc()->r_centers != centers) fail(kErrInternal);
-      vc()->n_alive -= removed;
-      if (vc()->n_alive < 0) fail(kErrInternal);
-      vc()->round = r + 1;
-      vc()->rebuilds_in_row = 0;
-      if (vc()->round > vc()->n + 1) fail(kErrInternal);
-    }
-    __syncthreads();
-    plan_round();
-  }
 };
 
 __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ RoundBuffers B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared& S = *reinterpret_cast<Shared*>(smem_raw);
-  K k{B, B.ctl, &S, gridDim.x, Tally{0, 0, 0, 0, 0, 0, 0}};
+  K k{B, B.ctl, &S, gridDim.x, 0u, Tally{0, 0, 0, 0, 0, 0, 0}};
   for (int i = threadIdx.x; i < kHist; i += blockDim.x) S.hist[i] = 0;
   if ((threadIdx.x & 31) == 0) S.app[threadIdx.x >> 5].n = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    for (int i = 0; i < 8; ++i) S.co.ph_ns[i] = 0;
+    S.co.t0 = globaltimer_ns();
+  }
   __syncthreads();
   Ctl* C = B.ctl;
-  volatile Ctl* V = B.ctl;
-  const int algo = V->algo;
-  if (blockIdx.x == 0 && threadIdx.x == 0) V->ph_t0 = globaltimer_ns();
+  const int algo = vload(&C->algo);
+  if (!k.sync(7, [&] { k.co_init(); })) goto out;
 
   for (;;) {
-    if (vload(&C->need_rebuild)) {
-      if (!k.rebuild()) return;
+    if (S.plan.state == kDone) break;
+    if (S.plan.state == kRebuild) {
+      if (!k.rebuild()) goto out;
       continue;
     }
-    if (vload(&C->done)) break;
-    if (!k.select(algo)) return;
-    const int32_t th = vload(&C->th);
-    bool lead;
-    if (algo == kAlgoCW) {
-      k.attach_from_actives(false, th);
-      k.hist_flush(th);
-      lead = k.arrive(4);
-      if (!k.finish(lead)) return;
-    } else {
-      k.c4_detect();
-      lead = k.arrive(4);
-      if (!k.finish(lead)) return;
-      k.c4_classify();
-      k.attach_from_actives(true, th);
-      k.hist_flush(th);
-      lead = k.arrive(4);
-      if (lead && threadIdx.x == 0) {
-        const unsigned long long p = V->blk_pack;
-        V->b_n = (int64_t)(p >> kPackShift);
-        V->b_E = (int64_t)(p & kPackEdgeMask);
-        V->undecided = V->b_n;
-        V->fix_iter = 0;
-        V->r_edges += 2 * V->b_E;          // blocked attach / pull pass, first fixpoint scan
-      }
-      if (!k.finish(lead)) return;
-      if (vload(&C->b_n) > 0) {
-        k.c4_blocked_init();
-        lead = k.arrive(5);
-        if (!k.finish(lead)) return;
-        while (vload(&C->undecided) > 0) {
-          k.c4_fix_scan();
-          lead = k.arrive(5);
-          if (lead && threadIdx.x == 0) V->undecided = 0;
-          if (!k.finish(lead)) return;
-          const long long left = block_sum<int64_t>(k.c4_fix_decide(), S.scr);
-          if (threadIdx.x == 0 && left) atomicAdd(reinterpret_cast<unsigned long long*>(&C->undecided),
-                                                  (unsigned long long)left);
-          lead = k.arrive(5);
-          if (lead && threadIdx.x == 0) {
-            V->fix_iter += 1;
-            if (V->fix_iter > 1) V->r_edges += V->b_E;
-            if (V->fix_iter > V->b_n + 1) { k.fail(kErrInternal); V->undecided = 0; }
-          }
-          if (!k.finish(lead)) return;
-        }
-        k.c4_blocked_attach(th);
+    if (!k.select(algo)) goto out;
+    {
+      const int32_t th = S.plan.th;
+      if (algo == kAlgoCW) {
+        k.attach_from_actives(false, th);
         k.hist_flush(th);
-        lead = k.arrive(5);
-        if (!k.finish(lead)) return;
-        k.c4_pull_finalize();
-        lead = k.arrive(5);
-        if (!k.finish(lead)) return;
+        if (!k.sync(4, [&] { k.co_lists_ready(); })) goto out;
+      } else {
+        k.c4_detect();
+        if (!k.sync(4)) goto out;
+        k.c4_classify();
+        k.attach_from_actives(true, th);
+        k.hist_flush(th);
+        if (!k.sync(4, [&] {
+              if (threadIdx.x == 0) {
+                const unsigned long long pk = vload(&C->blk_pack);
+                S.plan.b_n = (int64_t)(pk >> kPackShift);
+                S.plan.b_E = (int64_t)(pk & kPackEdgeMask);
+                S.plan.undecided = S.plan.b_n;
+                S.co.fix_iter = 0;
+                S.co.r_edges += 2 * S.plan.b_E;       // first fixpoint scan, blocked attach / pull
+              }
+              k.co_lists_ready();
+            }))
+          goto out;
+        if (S.plan.b_n > 0) {
+          k.c4_blocked_init();
+          if (!k.sync(5, [&] {
+                if (threadIdx.x == 0) C->undecided = 0;
+              }))
+            goto out;
+          while (S.plan.undecided > 0) {
+            k.c4_fix_scan();
+            if (!k.sync(5)) goto out;
+            const long long left = block_sum<int64_t>(k.c4_fix_decide(), S.scr);
+            if (threadIdx.x == 0 && left)
+              atomicAdd(reinterpret_cast<unsigned long long*>(&C->undecided), (unsigned long long)left);
+            if (!k.sync(5, [&] {
+                  if (threadIdx.x == 0) {
+                    S.plan.undecided = vload(&C->undecided);
+                    C->undecided = 0;
+                    S.co.fix_iter += 1;
+                    if (S.co.fix_iter > 1) S.co.r_edges += S.plan.b_E;
+                    if (S.co.fix_iter > S.plan.b_n + 1) { k.fail(kErrInternal); S.plan.undecided = 0; }
+                  }
+                }))
+              goto out;
+          }
+          k.c4_blocked_attach(th);
+          k.hist_flush(th);
+          if (!k.sync(5)) goto out;
+          k.c4_pull_finalize();
+          if (!k.sync(5, [&] { k.co_lists_ready(); })) goto out;
+        }
       }
+      k.decrement(th);
+      k.hist_flush(th);
+      k.flush_round_tallies();
+      if (!k.sync(6, [&] { k.co_end_round(); k.rebuild_plan_fields(); })) goto out;
     }
-    k.decrement(th);
-    k.hist_flush(th);
-    k.flush_round_tallies();
-    lead = k.arrive(6);
-    if (lead) k.end_round();
-    if (!k.finish(lead)) return;
+  }
+out:
+  // coordinator: results for the host
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    C->round = S.co.round;
+    C->n_alive = S.co.n_alive;
+    C->done = S.plan.state == kDone ? 1 : 0;
+    for (int i = 0; i < 8; ++i) C->ph_ns[i] = S.co.ph_ns[i];
   }
 }
 
@@ -817,19 +1017,8 @@ __global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm) {
     Ctl* C = B.ctl;
     C->algo = algo;
     C->eps_ppm = eps_ppm;
-    C->n = n;
-    C->nnz = B.nnz;
-    C->max_deg = B.max_deg;
     C->n_alive = n;
-    C->cursor = 0;
-    C->al_len = n;
-    C->al_identity = 1;
-    C->al_sel = 0;
-    C->th = B.max_deg + 1;       // nothing tracked: the first rebuild fills the table
-    C->top = B.max_deg;
-    C->need_rebuild = n > 0 ? 1 : 0;
     C->done = n > 0 ? 0 : 1;
-    C->r0 = -1;
   }
 }
 
@@ -854,7 +1043,7 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   size_t b = 0;
   b += align_up(sizeof(Ctl));
   b += align_up(8 * nn);                 // st
-  b += 2 * align_up(4 * nn);             // al0, al1
+  b += 2 * align_up(8 * nn);             // al0, al1
   b += 2 * align_up(4 * nn) + 2 * align_up(8 * nn);   // act_v, act_r, act_e, act_d
   b += align_up(4 * nn) + 2 * align_up(8 * nn);       // new_v, new_e, new_d
   b += align_up(4 * nn);                 // size
@@ -872,8 +1061,8 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   auto take = [&](size_t bytes) { char* q = p; p += align_up(bytes); return q; };
   B->ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
   B->st = reinterpret_cast<unsigned long long*>(take(8 * nn));
-  B->al0 = reinterpret_cast<int32_t*>(take(4 * nn));
-  B->al1 = reinterpret_cast<int32_t*>(take(4 * nn));
+  B->al0 = reinterpret_cast<int2*>(take(8 * nn));
+  B->al1 = reinterpret_cast<int2*>(take(8 * nn));
   B->act_v = reinterpret_cast<int32_t*>(take(4 * nn));
   B->act_r = reinterpret_cast<int32_t*>(take(4 * nn));
   B->act_e = reinterpret_cast<int64_t*>(take(8 * nn));
