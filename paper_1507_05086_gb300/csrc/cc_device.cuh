@@ -206,11 +206,13 @@ __device__ __forceinline__ T block_max(T x, T* scratch) {
 // ---------------------------------------------------------------------------
 constexpr int kLbsK = 4;
 constexpr int kLbsW = 32 * kLbsK;
-constexpr int kLbsBatches = 4;
+constexpr int kLbsBatches = 8;
 
 struct LbsWarp {
   int32_t mark[kLbsW];   // relative item index per position
   int32_t rel[kLbsW];    // item start relative to the batch base
+  int32_t next;          // relative index of the item starting the next batch
+  int32_t pad;
 };
 
 // One batch of kLbsW virtual edges as seen by one lane.
@@ -255,7 +257,11 @@ __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  constexpr int64_t kChunk = (int64_t)kLbsW * kLbsBatches;
+  // up to kLbsBatches batches per chunk, fewer when the list is short, so
+  // that short lists still spread over many warps
+  int64_t nb = E / (nwarps * (int64_t)kLbsW * 2);
+  nb = nb < 1 ? 1 : (nb > kLbsBatches ? kLbsBatches : nb);
+  const int64_t kChunk = (int64_t)kLbsW * nb;
   for (int64_t c0 = gwarp * kChunk; c0 < E; c0 += nwarps * kChunk) {
     int64_t j0 = warp_upper_bound(epos, nitems, c0) - 1;
     const int64_t cend = c0 + kChunk < E ? c0 + kChunk : E;
@@ -267,6 +273,7 @@ __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems
         s[t] = jj < nitems ? ldcg(epos + jj) : INT64_MAX;
         ws->mark[lane + 32 * t] = -1;
       }
+      if (lane == 0) ws->next = -1;
       __syncwarp();
 #pragma unroll
       for (int t = 0; t < kLbsK; ++t) {
@@ -274,6 +281,8 @@ __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems
         if (s[t] < base + kLbsW) {
           ws->rel[i] = (int32_t)(s[t] - base);
           if (s[t] >= base) ws->mark[s[t] - base] = i;
+        } else if (s[t] == base + kLbsW) {
+          ws->next = i;                  // the item that starts the next batch
         }
       }
       __syncwarp();
@@ -313,12 +322,16 @@ __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems
         if (base + p < cend) L.valid |= 1u << t;
       }
       const int last = ws->mark[kLbsW - 1];
+      const int nxt = ws->next;
       f(L);
       __syncwarp();
       // next batch: the item holding its first edge is the last item of this
-      // batch or, when an item starts exactly at the next base, its successor
-      j0 += last;
-      if (j0 + 1 < nitems && ldcg(epos + j0 + 1) <= base + kLbsW) ++j0;
+      // batch or, when an item starts exactly at the next base, that item (the
+      // item after `last` is always among the ones loaded here unless `last`
+      // is the final loaded slot, in which case one load decides)
+      if (nxt >= 0) j0 += nxt;
+      else if (last == kLbsW - 1 && j0 + kLbsW < nitems && ldcg(epos + j0 + kLbsW) <= base + kLbsW) j0 += kLbsW;
+      else j0 += last;
     }
   }
 }

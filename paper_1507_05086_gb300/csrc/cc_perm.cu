@@ -4,8 +4,9 @@
 // uniform 64-bit values, so a two-level sort suffices:
 //   1. bucket vertices by the top b key bits (b chosen so a bucket holds about
 //      384-768 vertices): a histogram, an exclusive scan and a scatter;
-//   2. sort each bucket in shared memory by the full (key, v) with a bitonic
-//      network and write its slice of order[].
+//   2. sort each bucket in shared memory by the full (key, v): a counting sort
+//      on the next 10 key bits, then an insertion sort per sub-bucket of
+//      about one element, and write its slice of order[].
 // Keys are recomputed from v wherever needed instead of being stored, so the
 // only global traffic is 4 bytes per vertex scattered and 4+4 bytes per vertex
 // read and written by the bucket sort.  A bucket larger than the shared-memory
@@ -19,7 +20,7 @@
 namespace ccg {
 namespace {
 
-constexpr int kBucketCap = 4096;      // vertices per bucket sorted in shared memory
+constexpr int kBucketCap = 1536;      // vertices per bucket sorted in shared memory
 constexpr int kSortThreads = 512;
 constexpr int kMaxOverflow = 1023;    // buckets above capacity handled by the fallback
 
@@ -65,12 +66,24 @@ __device__ __forceinline__ bool kv_less(uint64_t ka, int32_t va, uint64_t kb, in
   return ka < kb || (ka == kb && va < vb);
 }
 
-// One block per bucket (grid-stride): bitonic sort of (key, v) in shared memory.
+// One block per bucket (grid-stride).  Inside a bucket the keys share their
+// top `bits` bits and the next kSubBits bits are still uniform, so a counting
+// sort on those bits spreads the bucket over kSub sub-buckets of about one
+// element each; one thread then finishes each sub-bucket with an insertion
+// sort on the full (key, v).
+constexpr int kSubBits = 10;
+constexpr int kSub = 1 << kSubBits;
+
 __global__ void __launch_bounds__(kSortThreads)
-k_bucket_sort(uint64_t seed, int64_t nb, const int64_t* __restrict__ start, const int32_t* __restrict__ tmp,
-              int32_t* __restrict__ order, int* __restrict__ overflow) {
+k_bucket_sort(uint64_t seed, int bits, int64_t nb, const int64_t* __restrict__ start,
+              const int32_t* __restrict__ tmp, int32_t* __restrict__ order, int* __restrict__ overflow) {
   __shared__ uint64_t sk[kBucketCap];
   __shared__ int32_t sv[kBucketCap];
+  __shared__ uint64_t ok_[kBucketCap];
+  __shared__ int32_t ov[kBucketCap];
+  __shared__ int32_t cnt[kSub + 1];
+  __shared__ int64_t scr[33];
+  const int shift = 64 - bits - kSubBits;
   for (int64_t b = blockIdx.x; b < nb; b += gridDim.x) {
     const int64_t s0 = start[b], len = start[b + 1] - s0;
     if (len <= 0) continue;
@@ -81,38 +94,54 @@ k_bucket_sort(uint64_t seed, int64_t nb, const int64_t* __restrict__ start, cons
       }
       continue;
     }
-    int p2 = 1;
-    while (p2 < len) p2 <<= 1;
-    for (int i = threadIdx.x; i < p2; i += blockDim.x) {
-      if (i < len) {
-        int32_t v = tmp[s0 + i];
-        sv[i] = v;
-        sk[i] = perm_key(seed, (uint64_t)v);
-      } else {
-        sv[i] = INT32_MAX;
-        sk[i] = UINT64_MAX;
+    for (int i = threadIdx.x; i < kSub; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const int32_t v = tmp[s0 + i];
+      const uint64_t k = perm_key(seed, (uint64_t)v);
+      sv[i] = v;
+      sk[i] = k;
+      atomicAdd(&cnt[(int)((k >> shift) & (kSub - 1))], 1);
+    }
+    __syncthreads();
+    // exclusive scan of the sub-bucket counts (two per thread)
+    {
+      const int i0 = threadIdx.x * 2;
+      const int c0 = i0 < kSub ? cnt[i0] : 0, c1 = i0 + 1 < kSub ? cnt[i0 + 1] : 0;
+      int64_t tot;
+      const int64_t ex = block_exclusive_sum<int64_t>(c0 + c1, scr, &tot);
+      if (i0 < kSub) cnt[i0] = (int)ex;
+      if (i0 + 1 < kSub) cnt[i0 + 1] = (int)ex + c0;
+      if (threadIdx.x == 0) cnt[kSub] = (int)tot;
+    }
+    __syncthreads();
+    // scatter into sub-buckets (arbitrary order inside a sub-bucket); the
+    // counters end at the next sub-bucket's start
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const uint64_t k = sk[i];
+      const int pos = atomicAdd(&cnt[(int)((k >> shift) & (kSub - 1))], 1);
+      ok_[pos] = k;
+      ov[pos] = sv[i];
+    }
+    __syncthreads();
+    // sub-bucket q now spans [q == 0 ? 0 : cnt[q-1], cnt[q]): insertion sort
+    for (int q = threadIdx.x; q < kSub; q += blockDim.x) {
+      const int lo = q == 0 ? 0 : cnt[q - 1], hi = cnt[q];
+      for (int i = lo + 1; i < hi; ++i) {
+        const uint64_t k = ok_[i];
+        const int32_t v = ov[i];
+        int j = i - 1;
+        while (j >= lo && kv_less(k, v, ok_[j], ov[j])) {
+          ok_[j + 1] = ok_[j];
+          ov[j + 1] = ov[j];
+          --j;
+        }
+        ok_[j + 1] = k;
+        ov[j + 1] = v;
       }
     }
     __syncthreads();
-    for (int kk = 2; kk <= p2; kk <<= 1) {
-      for (int j = kk >> 1; j > 0; j >>= 1) {
-        for (int t = threadIdx.x; t < (p2 >> 1); t += blockDim.x) {
-          // index pair (i, i ^ j) with i having bit j clear
-          const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-          const int l = i | j;
-          const bool up = (i & kk) == 0;
-          const uint64_t ki = sk[i], kl = sk[l];
-          const int32_t vi = sv[i], vl = sv[l];
-          const bool swap = up ? kv_less(kl, vl, ki, vi) : kv_less(ki, vi, kl, vl);
-          if (swap) {
-            sk[i] = kl; sk[l] = ki;
-            sv[i] = vl; sv[l] = vi;
-          }
-        }
-        __syncthreads();
-      }
-    }
-    for (int i = threadIdx.x; i < len; i += blockDim.x) order[s0 + i] = sv[i];
+    for (int i = threadIdx.x; i < len; i += blockDim.x) order[s0 + i] = ov[i];
     __syncthreads();
   }
 }
@@ -182,7 +211,7 @@ cudaError_t launch_permutation(int64_t n, uint64_t seed, int32_t* order, void* w
   k_bucket_scan<<<1, 1024, 0, stream>>>(count, nb, start, cursor);
   k_bucket_scatter<<<grid, 256, 0, stream>>>(n, seed, bits, cursor, tmp);
   const int sgrid = (int)(nb < (int64_t)num_sms * 4 ? nb : (int64_t)num_sms * 4);
-  k_bucket_sort<<<sgrid, kSortThreads, 0, stream>>>(seed, nb, start, tmp, order, overflow);
+  k_bucket_sort<<<sgrid, kSortThreads, 0, stream>>>(seed, bits, nb, start, tmp, order, overflow);
   // The fallback kernel returns at once when no bucket overflowed, so it
   // always runs; this keeps the host free of a sync.
   k_bucket_sort_large<<<num_sms, 256, 0, stream>>>(seed, overflow, start, tmp, order, err);

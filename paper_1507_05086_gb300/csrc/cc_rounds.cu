@@ -26,9 +26,9 @@
 // Residual degrees live in the low word, so the decrement that follows the
 // removal of a vertex is a 32-bit atomic on the same cache sector the alive
 // test just read.  Delta_i (max residual degree, exact every round) comes
-// from a count-per-degree table kept only for degrees >= th; when no tracked
-// vertex is left, a rebuild rescans the alive list, compacts it, lowers th
-// and refills the table.
+// from a count-per-degree table of every degree >= 1 (low bins aggregated in
+// shared memory), walked down from the previous maximum; a rebuild rescans
+// and compacts the alive list when most of its entries are dead.
 //
 // Every adjacency pass is edge-balanced (lbs_for_each), so hub rows of
 // power-law graphs are split across many warps.
@@ -412,8 +412,9 @@ struct K {
             Coord& c = co();
             if (tot != c.n_alive) fail(kErrInternal);
             c.top = (int32_t)D;
-            const int32_t th = (int32_t)(D >> 2);
-            c.th = th < 1 ? 1 : th;
+            // every degree >= 1 is tracked, so later rebuilds only compact the
+            // alive list (Delta never needs a rescan)
+            c.th = 1;
             S->plan.th = c.th;
             S->plan.take = tot;
           }
