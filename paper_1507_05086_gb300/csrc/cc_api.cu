@@ -316,6 +316,8 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
   b.off = g->off;
   b.col = g->col;
   b.order = g->order;
+  b.nz_static = g->nz_row;
+  b.nz_n = g->nz_n;
   b.stats = g->stats_dev;
   b.stats_cap = stats_cap;
   CC_TRY(cudaMemsetAsync(g->perm_err, 0, sizeof(int), s));

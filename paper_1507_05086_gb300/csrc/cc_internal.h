@@ -46,6 +46,7 @@ struct Ctl {
   unsigned long long act_pack, new_pack, blk_pack;
   long long r_centers, r_attached, r_noncenter, r_blocked;
   long long undecided;
+  unsigned long long h_pack;      // heavy-list appends
   int32_t r0;
   int64_t cursor_next;
   // objective tallies: member-center edges, member-member edges (counted from
@@ -80,7 +81,11 @@ struct RoundBuffers {
   int64_t* new_e;
   int64_t* new_d;
   int32_t* size;
-  int32_t* cnt;                // degree-count table, max_deg + 2 + histogram window
+  int32_t* hv;                 // heavy list (Delta candidates)
+  int32_t* nz0;                // alive non-isolated vertices (double buffer)
+  int32_t* nz1;
+  const int32_t* nz_static;    // the graph's non-isolated vertices
+  int64_t nz_n;
   uint8_t* blk_flag;
   uint8_t* hit_c;
   uint8_t* hit_p;

@@ -24,11 +24,15 @@
 // one compare-then-atomicMin does rule 2 and skips dead and active vertices.
 //
 // Residual degrees live in the low word, so the decrement that follows the
-// removal of a vertex is a 32-bit atomic on the same cache sector the alive
-// test just read.  Delta_i (max residual degree, exact every round) comes
-// from a count-per-degree table of every degree >= 1 (low bins aggregated in
-// shared memory), walked down from the previous maximum; a rebuild rescans
-// and compacts the alive list when most of its entries are dead.
+// removal of a vertex is a fire-and-forget 32-bit atomic on the same cache
+// sector the alive test just read.  Delta_i (max residual degree, exact every
+// round) comes from a heavy list H: every alive vertex whose degree was >= tau
+// when H was built.  Degrees only fall, so if the largest current degree in H
+// is still >= tau it is the maximum over the whole graph; otherwise a rebuild
+// scans the compact list of alive non-isolated vertices, takes the exact
+// maximum D, sets tau = D/2 and refills H.  No work per decrement.
+// The rank-ordered alive list used for selection is compacted separately when
+// most of its live range is dead.
 //
 // Every adjacency pass is edge-balanced (lbs_for_each), so hub rows of
 // power-law graphs are split across many warps.
@@ -42,12 +46,12 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kHist = 2048;                  // shared-memory window of the degree table
 constexpr int kScanU = 4;                    // alive-list entries per thread per scan step
 constexpr int32_t kAliveHi = 0x7FFFFFFF;
 constexpr uint32_t kUndecided = 0, kCenter = 1, kNonCenter = 2;
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
-constexpr int kRun = 0, kDone = 1, kRebuild = 2, kAbort = 3;
+constexpr int kRun = 0, kDone = 1, kRebuild = 2, kAbort = 3, kRebuildDelta = 4, kScanH = 5;
+constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
 
 __device__ __forceinline__ int32_t hi_of(unsigned long long x) { return (int32_t)(x >> 32); }
 __device__ __forceinline__ uint32_t lo_of(unsigned long long x) { return (uint32_t)x; }
@@ -67,8 +71,10 @@ __device__ __forceinline__ void atom_add_release(unsigned* p, unsigned v) {
 struct Coord {
   int64_t n, n_alive, cursor, al_len, k, round, stats_cap, eps_ppm;
   int64_t need, win_lo, win_len, r_edges, fix_iter;
-  int32_t th, top, delta, max_deg;
+  int64_t h_len, nz_len, nz_total;
+  int32_t tau, delta, max_deg, d_new;
   int algo, al_sel, al_ident, rebuilds_in_row;
+  int nz_sel, nz_static;
   unsigned long long t0;
   unsigned long long ph_ns[8];
 };
@@ -81,7 +87,6 @@ struct Shared {
   int dec;
   int64_t scr[33];
   int64_t bcast[8];
-  int32_t hist[kHist];
   LbsWarp lbs[kWarps];
   AppendBuf app[kWarps];
 };
@@ -168,25 +173,6 @@ struct K {
     return sync(cat, [] {});
   }
 
-  // ---------------- degree-count table --------------------------------------
-  __device__ void hist_add(int32_t th, uint32_t d, int delta) {
-    if ((int64_t)d < th) return;
-    const int64_t i = (int64_t)d - th;
-    if (i < kHist) atomicAdd(&S->hist[i], delta);
-    else atomicAdd(&B.cnt[d], delta);
-  }
-  __device__ void hist_flush(int32_t th) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < kHist; i += blockDim.x) {
-      const int32_t v = S->hist[i];
-      if (v != 0) {
-        if ((int64_t)th + i <= (int64_t)B.max_deg) atomicAdd(&B.cnt[th + i], v);
-        S->hist[i] = 0;
-      }
-    }
-    __syncthreads();
-  }
-
   __device__ RowList new_list() const { return RowList{B.new_v, B.new_e, B.new_d, nullptr, &C->new_pack}; }
   __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, nullptr, &C->blk_pack}; }
   __device__ LbsWarp* lbs_ws() const { return &S->lbs[threadIdx.x >> 5]; }
@@ -256,8 +242,11 @@ struct K {
       c.al_ident = 1;
       c.al_sel = 0;
       c.max_deg = B.max_deg;
-      c.th = B.max_deg + 1;       // nothing tracked: the first rebuild fills the table
-      c.top = B.max_deg;
+      c.tau = 0x7FFFFFFF;         // empty heavy list: the first round rebuilds it
+      c.h_len = 0;
+      c.nz_len = B.nz_n;          // non-isolated vertices, from the graph
+      c.nz_static = 1;
+      c.nz_sel = 0;
       c.round = 0;
       c.rebuilds_in_row = 0;
       c.algo = vload(&C->algo);
@@ -265,80 +254,102 @@ struct K {
       c.stats_cap = B.stats_cap;
       Plan& p = S->plan;
       p = Plan{};
-      p.state = B.n > 0 ? kRebuild : kDone;
       p.r0 = -1;
     }
     __syncthreads();
-    rebuild_plan_fields();
+    co_decide_delta();
   }
 
-  // Sets Delta, k and the first selection window, or asks for a rebuild.
-  __device__ void plan_round() {
+  // Coordinator: with Delta known, set k and the first selection window.
+  __device__ void plan_selection(int32_t delta) {
+    if (threadIdx.x == 0) {
+      Coord& c = co();
+      Plan& p = S->plan;
+      int64_t k;
+      if (delta <= 0) k = c.n_alive;
+      else {
+        const unsigned long long num = (unsigned long long)c.eps_ppm * (unsigned long long)c.n_alive;
+        const unsigned long long den = 1000000ull * (unsigned long long)delta;
+        k = (int64_t)((num + den - 1) / den);
+        if (k < 1) k = 1;
+        if (k > c.n_alive) k = c.n_alive;
+      }
+      c.delta = delta;
+      c.k = k;
+      c.need = k;
+      c.win_lo = c.cursor;
+      const int64_t avail = c.al_len - c.cursor;
+      const int64_t est = (int64_t)((double)k * (double)avail / (double)c.n_alive * 1.05) + 256;
+      c.win_len = est < avail ? est : avail;
+      c.r_edges = 0;
+      C->act_pack = 0; C->new_pack = 0; C->blk_pack = 0;
+      C->r_centers = 0; C->r_attached = 0; C->r_noncenter = 0; C->r_blocked = 0;
+      C->r0 = -1;
+      p.state = kRun;
+      p.k = k;
+      p.need = k;
+      p.win_lo = c.win_lo;
+      p.win_len = c.win_len;
+      p.th = 0;
+      p.r0 = -1;
+      p.al_sel = c.al_sel;
+      p.al_ident = c.al_ident;
+    }
+    __syncthreads();
+  }
+
+  // Coordinator, at a round boundary: finish, compact the alive list, or get
+  // Delta from the heavy list (inline when short, else by a grid scan), or
+  // rebuild the heavy list.
+  __device__ void co_decide_delta() {
     Coord& c = co();
     Plan& p = S->plan;
     if (threadIdx.x == 0) {
-      int dec = 0;
-      if (c.n_alive <= 0) { p.state = kDone; dec = 1; }
-      else if (!c.al_ident && c.al_len - c.cursor > 4 * c.n_alive + 65536) { p.state = kRebuild; dec = 1; }
+      int dec = 1;
+      if (c.n_alive <= 0) p.state = kDone;
+      else if (!c.al_ident && c.al_len - c.cursor > 4 * c.n_alive + 65536) {
+        p.state = kRebuild;               // compact the alive list first
+        p.al_sel = c.al_sel;
+        p.al_ident = c.al_ident;
+        p.win_lo = c.cursor;
+        p.win_len = c.al_len - c.cursor;
+      } else if (c.nz_len == 0) {
+        dec = 2;                          // every alive vertex is isolated: Delta = 0
+      } else if (c.h_len == 0 || c.h_len > kInlineH) {
+        if (c.h_len == 0) { p.state = kRebuildDelta; set_nz_plan(); }
+        else { p.state = kScanH; p.win_lo = 0; p.win_len = c.h_len; }
+      } else {
+        dec = 0;                          // scan the short heavy list here
+      }
       S->dec = dec;
     }
     __syncthreads();
+    if (S->dec == 2) { plan_selection(0); return; }
     if (S->dec) return;
-    // walk the degree table down from `top`, four bins per thread per step
-    const int32_t th = c.th;
-    int32_t tt = c.top;
-    int32_t found = -1;
-    while (tt >= th) {
-      int32_t hit = -1;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int32_t d = tt - (int32_t)(threadIdx.x * 4 + q);
-        if (d >= th && hit < 0 && ldcg(B.cnt + d) > 0) hit = d;
-      }
-      found = (int32_t)block_max<int64_t>(hit, S->scr);
-      if (found >= 0) break;
-      tt -= 4 * (int32_t)blockDim.x;
+    int64_t mx = -1;
+    for (int64_t i = threadIdx.x; i < c.h_len; i += blockDim.x) {
+      const unsigned long long x = ldcg(B.st + ldcg(B.hv + i));
+      if (hi_of(x) == kAliveHi) mx = (int64_t)lo_of(x) > mx ? (int64_t)lo_of(x) : mx;
     }
-    if (threadIdx.x == 0) {
-      int32_t delta = 0;
-      bool ok = true;
-      if (found >= 0) { delta = found; c.top = found; }
-      else if (th <= 1) { delta = 0; c.top = 0; }
-      else { p.state = kRebuild; ok = false; }
-      if (ok) {
-        int64_t k;
-        if (delta <= 0) k = c.n_alive;
-        else {
-          const unsigned long long num = (unsigned long long)c.eps_ppm * (unsigned long long)c.n_alive;
-          const unsigned long long den = 1000000ull * (unsigned long long)delta;
-          k = (int64_t)((num + den - 1) / den);
-          if (k < 1) k = 1;
-          if (k > c.n_alive) k = c.n_alive;
-        }
-        c.delta = delta;
-        c.k = k;
-        c.need = k;
-        c.win_lo = c.cursor;
-        const int64_t avail = c.al_len - c.cursor;
-        const int64_t est = (int64_t)((double)k * (double)avail / (double)c.n_alive * 1.05) + 256;
-        c.win_len = est < avail ? est : avail;
-        c.r_edges = 0;
-        // counters of the round
-        C->act_pack = 0; C->new_pack = 0; C->blk_pack = 0;
-        C->r_centers = 0; C->r_attached = 0; C->r_noncenter = 0; C->r_blocked = 0;
-        C->r0 = -1;
-        p.state = kRun;
-        p.k = k;
-        p.need = k;
-        p.win_lo = c.win_lo;
-        p.win_len = c.win_len;
-        p.th = c.th;
-        p.r0 = -1;
-        p.al_sel = c.al_sel;
-        p.al_ident = c.al_ident;
-      }
-    }
+    mx = block_max<int64_t>(mx, S->scr);
+    co_after_heavy((int32_t)mx);
+  }
+
+  // Coordinator: the largest current degree in the heavy list is mx (-1 if
+  // none is alive).  It is the global maximum when it is still >= tau.
+  __device__ void co_after_heavy(int32_t mx) {
+    if (threadIdx.x == 0) S->dec = mx >= co().tau ? 1 : 0;
     __syncthreads();
+    if (S->dec) { plan_selection(mx); return; }
+    if (threadIdx.x == 0) { S->plan.state = kRebuildDelta; set_nz_plan(); }
+    __syncthreads();
+  }
+
+  __device__ void set_nz_plan() {
+    Coord& c = co();
+    S->plan.win_lo = 0;
+    S->plan.win_len = c.nz_static ? c.nz_len : c.nz_len;
+    S->plan.pad0 = (c.nz_static ? 2 : 0) | c.nz_sel;
   }
 
   // Statistics and n_i update after the removal phase, then the next plan.
@@ -372,83 +383,61 @@ struct K {
       if (c.round > c.n + 1) fail(kErrInternal);
     }
     __syncthreads();
-    plan_round();
+    co_decide_delta();
   }
 
-  // ---------------- rebuild: compact the alive list, refill the table -------
+  // ---------------- alive-list compaction -----------------------------------
   __device__ bool rebuild() {
     const int sel = P().al_sel, ident = P().al_ident;
     const int64_t lo = P().win_lo, len = P().win_len;     // the live part of the list
-    const int32_t top = P().th;                            // zero bins [0, top + 1 + kHist)
-    // A: zero the table, count alive and find the largest degree per block
-    const int64_t zhi = (int64_t)top + 1 + kHist;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < zhi && i <= (int64_t)B.max_deg + 1 + kHist;
-         i += (int64_t)G * blockDim.x)
-      B.cnt[i] = 0;
     int64_t s, e;
     slice(lo, len, &s, &e);
-    int64_t cnt = 0, mx = 0;
+    int64_t cnt = 0;
     for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
       int2 a[kScanU];
-      unsigned long long x[kScanU];
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
         const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
         a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
       }
 #pragma unroll
-      for (int q = 0; q < kScanU; ++q) x[q] = a[q].y >= 0 ? ldcg(B.st + a[q].y) : 0;
-#pragma unroll
       for (int q = 0; q < kScanU; ++q)
-        if (a[q].y >= 0 && hi_of(x[q]) == kAliveHi) { ++cnt; mx = lo_of(x[q]) > mx ? lo_of(x[q]) : mx; }
+        cnt += (a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi) ? 1 : 0;
     }
     cnt = block_sum<int64_t>(cnt, S->scr);
-    mx = block_max<int64_t>(mx, S->scr);
-    if (threadIdx.x == 0) { B.blk_a[blockIdx.x] = cnt; B.blk_b[blockIdx.x] = mx; }
+    if (threadIdx.x == 0) B.blk_a[blockIdx.x] = cnt;
     if (!sync(0, [&] {
           const int64_t tot = prefix_blocks();
-          const int64_t D = max_blocks();
           if (threadIdx.x == 0) {
-            Coord& c = co();
-            if (tot != c.n_alive) fail(kErrInternal);
-            c.top = (int32_t)D;
-            // every degree >= 1 is tracked, so later rebuilds only compact the
-            // alive list (Delta never needs a rescan)
-            c.th = 1;
-            S->plan.th = c.th;
+            if (tot != co().n_alive) fail(kErrInternal);
             S->plan.take = tot;
           }
         }))
       return false;
-    // B: stable compaction into the other buffer, refill the table
-    const int32_t th = P().th;
+    // stable compaction into the other buffer
     int2* dst = sel ? B.al0 : B.al1;
     int64_t run = ldcg(B.blk_a + blockIdx.x);
     for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
       int2 a[kScanU];
-      unsigned long long x[kScanU];
+      bool alive[kScanU];
+      int64_t mine = 0;
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
         const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
         a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
       }
-      int64_t mine = 0;
 #pragma unroll
-      for (int q = 0; q < kScanU; ++q) x[q] = a[q].y >= 0 ? ldcg(B.st + a[q].y) : 0;
-#pragma unroll
-      for (int q = 0; q < kScanU; ++q) mine += (a[q].y >= 0 && hi_of(x[q]) == kAliveHi) ? 1 : 0;
+      for (int q = 0; q < kScanU; ++q) {
+        alive[q] = a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi;
+        mine += alive[q] ? 1 : 0;
+      }
       int64_t tot;
       int64_t o = run + block_exclusive_sum<int64_t>(mine, S->scr, &tot);
 #pragma unroll
-      for (int q = 0; q < kScanU; ++q) {
-        if (a[q].y >= 0 && hi_of(x[q]) == kAliveHi) {
-          dst[o++] = a[q];
-          hist_add(th, lo_of(x[q]), 1);
-        }
-      }
+      for (int q = 0; q < kScanU; ++q)
+        if (alive[q]) dst[o++] = a[q];
       run += tot;
     }
-    hist_flush(th);
     return sync(1, [&] {
       if (threadIdx.x == 0) {
         Coord& c = co();
@@ -456,35 +445,156 @@ struct K {
         c.al_ident = 0;
         c.al_len = S->plan.take;
         c.cursor = 0;
-        // a rebuild always leaves a tracked vertex (or Delta = 0), so two in a
-        // row without a round in between mean the table is inconsistent
         c.rebuilds_in_row += 1;
-        if (c.rebuilds_in_row > 2) fail(kErrInternal);
+        if (c.rebuilds_in_row > 3) fail(kErrInternal);
       }
       __syncthreads();
-      plan_round();
-      rebuild_plan_fields();
+      co_decide_delta();
     });
   }
 
-  // When the plan asks for a rebuild, it carries the live part of the alive
-  // list and the zeroing bound in (win_lo, win_len, th).
-  __device__ void rebuild_plan_fields() {
-    if (threadIdx.x == 0 && S->plan.state == kRebuild) {
-      Coord& c = co();
-      S->plan.al_sel = c.al_sel;
-      S->plan.al_ident = c.al_ident;
-      S->plan.win_lo = c.cursor;
-      S->plan.win_len = c.al_len - c.cursor;
-      S->plan.th = c.top;
+  // ---------------- heavy list: per-round maximum ----------------------------
+  __device__ bool heavy_scan() {
+    int64_t s, e;
+    slice(0, P().win_len, &s, &e);
+    int64_t mx = -1;
+    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+      int32_t v[kScanU];
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+        v[q] = i < e ? ldcg(B.hv + i) : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        if (v[q] < 0) continue;
+        const unsigned long long x = ldcg(B.st + v[q]);
+        if (hi_of(x) == kAliveHi) mx = (int64_t)lo_of(x) > mx ? (int64_t)lo_of(x) : mx;
+      }
     }
-    __syncthreads();
+    mx = block_max<int64_t>(mx, S->scr);
+    if (threadIdx.x == 0) B.blk_b[blockIdx.x] = mx;
+    return sync(0, [&] {
+      const int64_t m = max_blocks_signed();
+      co_after_heavy((int32_t)m);
+    });
+  }
+
+  // ---------------- heavy list rebuild ------------------------------------------
+  // A: over the non-isolated alive list, count the vertices that are still
+  // alive with a degree > 0 and find the largest degree D.  B: compact that
+  // list and put every survivor with degree >= tau = max(1, D/2) on the heavy
+  // list.  Delta = D exactly.
+  __device__ int32_t nz_at(int flags, int64_t i) const {
+    if (flags & 2) return __ldg(B.nz_static + i);
+    return ldcg(((flags & 1) ? B.nz1 : B.nz0) + i);
+  }
+
+  __device__ bool delta_rebuild() {
+    const int flags = P().pad0;
+    const int64_t len = P().win_len;
+    int64_t s, e;
+    slice(0, len, &s, &e);
+    int64_t cnt = 0, mx = 0;
+    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+      int32_t v[kScanU];
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+        v[q] = i < e ? nz_at(flags, i) : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        if (v[q] < 0) continue;
+        const unsigned long long x = ldcg(B.st + v[q]);
+        if (hi_of(x) == kAliveHi && lo_of(x) > 0) {
+          ++cnt;
+          mx = (int64_t)lo_of(x) > mx ? (int64_t)lo_of(x) : mx;
+        }
+      }
+    }
+    cnt = block_sum<int64_t>(cnt, S->scr);
+    mx = block_max<int64_t>(mx, S->scr);
+    if (threadIdx.x == 0) { B.blk_a[blockIdx.x] = cnt; B.blk_b[blockIdx.x] = mx; }
+    if (!sync(0, [&] {
+          const int64_t tot = prefix_blocks();
+          const int64_t D = max_blocks_signed();
+          if (threadIdx.x == 0) {
+            Coord& c = co();
+            c.nz_total = tot;
+            c.d_new = (int32_t)(D > 0 ? D : 0);
+            c.tau = D >= 2 ? (int32_t)(D >> 1) : 1;
+            S->plan.th = c.tau;
+            C->h_pack = 0;
+          }
+        }))
+      return false;
+    const int32_t tau = P().th;
+    int32_t* dst = (flags & 2) ? B.nz0 : ((flags & 1) ? B.nz0 : B.nz1);
+    int64_t run = ldcg(B.blk_a + blockIdx.x);
+    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+      int32_t v[kScanU];
+      uint32_t d[kScanU];
+      int64_t mine = 0, heavy = 0;
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+        v[q] = i < e ? nz_at(flags, i) : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        d[q] = 0;
+        if (v[q] < 0) continue;
+        const unsigned long long x = ldcg(B.st + v[q]);
+        if (hi_of(x) == kAliveHi) d[q] = lo_of(x);
+        mine += d[q] > 0 ? 1 : 0;
+        heavy += (d[q] > 0 && (int64_t)d[q] >= tau) ? 1 : 0;
+      }
+      int64_t tot, htot;
+      int64_t o = run + block_exclusive_sum<int64_t>(mine, S->scr, &tot);
+      int64_t ho = block_exclusive_sum<int64_t>(heavy, S->scr, &htot);
+      if (htot > 0) {
+        if (threadIdx.x == 0) S->bcast[0] = (int64_t)atomicAdd(&C->h_pack, (unsigned long long)htot);
+        __syncthreads();
+        ho += S->bcast[0];
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        if (d[q] == 0) continue;
+        dst[o++] = v[q];
+        if ((int64_t)d[q] >= tau) B.hv[ho++] = v[q];
+      }
+      run += tot;
+    }
+    return sync(1, [&] {
+      if (threadIdx.x == 0) {
+        Coord& c = co();
+        c.nz_sel = (flags & 2) ? 0 : ((flags & 1) ? 0 : 1);
+        c.nz_static = 0;
+        c.nz_len = c.nz_total;
+        c.h_len = (int64_t)vload(&C->h_pack);
+        c.rebuilds_in_row += 1;
+        if (c.rebuilds_in_row > 3) fail(kErrInternal);
+      }
+      __syncthreads();
+      plan_selection(co().d_new);
+    });
+  }
+
+  __device__ int64_t max_blocks_signed() {
+    int64_t m = -1;
+    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
+      const int64_t x = ldcg(B.blk_b + b);
+      m = x > m ? x : m;
+    }
+    return block_max<int64_t>(m, S->scr);
   }
 
   // ---------------- active-set selection (Alg. 2: A = next k alive of pi) ----
   // Called by every thread of the block for one tile of the window; entry q
   // of a thread is an active vertex (rank a[q].x, vertex a[q].y) when want[q].
-  __device__ void emit_actives(const int2* a, const bool* want, int algo, int32_t th) {
+  __device__ void emit_actives(const int2* a, const bool* want, int algo) {
     int64_t deg0[kScanU], row[kScanU];
     bool listed[kScanU];
     int64_t nl = 0, el = 0;
@@ -496,7 +606,6 @@ struct K {
       if (!want[q]) continue;
       const int32_t r = a[q].x, v = a[q].y;
       const uint32_t d = lo_of(ldcg(B.st + v));
-      hist_add(th, d, -1);                      // v leaves the graph this round
       B.size[r] = 0;
       if (d == 0) {                             // no alive neighbour: singleton center
         B.st[v] = word(r, 0);
@@ -570,7 +679,6 @@ struct K {
       // S2: emit the first `take` alive entries of the window
       const int64_t take = P().take, need = P().need;
       const bool first_window = P().r0 < 0;
-      const int32_t th = P().th;
       int64_t run = ldcg(B.blk_a + blockIdx.x);
       if (run < take) {
         for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
@@ -598,12 +706,11 @@ struct K {
               C->cursor_next = base + (int64_t)threadIdx.x * kScanU + q + 1;
             g += alive[q] ? 1 : 0;
           }
-          emit_actives(a, want, algo, th);
+          emit_actives(a, want, algo);
           run += tot;
           if (run >= take) break;           // uniform across the block
         }
       }
-      hist_flush(th);
       if (!sync(3, [&] {
             if (threadIdx.x == 0) {
               Coord& c = co();
@@ -652,7 +759,7 @@ struct K {
   // ---------------- createCluster: push a center's rank to its neighbours ----
   // Lanes with push == true try to attach u (state word x, read earlier) to
   // the center of rank r.  All 32 lanes must call it.
-  __device__ void attach_one(bool push, int32_t u, int32_t r, unsigned long long x, int32_t th) {
+  __device__ void attach_one(bool push, int32_t u, int32_t r, unsigned long long x) {
     bool fresh = false;
     uint32_t d_old = 0;
     const unsigned long long nv = (unsigned long long)(uint32_t)r << 32;
@@ -661,10 +768,7 @@ struct K {
           (unsigned long long)atomicMin(reinterpret_cast<long long*>(B.st + u), (long long)nv);
       if (hi_of(old) == kAliveHi) { fresh = true; d_old = lo_of(old); }
     }
-    if (fresh) {
-      hist_add(th, d_old, -1);
-      t.attached += 1;
-    }
+    if (fresh) t.attached += 1;
     // The center is the only alive neighbour of a fresh vertex of residual
     // degree 1: nothing to decrement, and no other center can reach it, so
     // its label is already final.
@@ -681,7 +785,7 @@ struct K {
     append_stage(app_buf(), want, u, row, len, new_list());
   }
 
-  __device__ void attach_from_actives(bool skip_blocked, int32_t th) {
+  __device__ void attach_from_actives(bool skip_blocked) {
     const int64_t an = P().act_n, aE = P().act_E;
     lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
       bool push[kLbsK];
@@ -699,7 +803,7 @@ struct K {
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) x[q] = push[q] ? ldcg(B.st + u[q]) : 0;
 #pragma unroll
-      for (int q = 0; q < kLbsK; ++q) attach_one(push[q], u[q], r[q], x[q], th);
+      for (int q = 0; q < kLbsK; ++q) attach_one(push[q], u[q], r[q], x[q]);
     });
     append_flush(app_buf(), new_list());
   }
@@ -807,7 +911,7 @@ struct K {
 
   // C4 after the fixpoint: blocked centers push, blocked non-centers pull the
   // lowest center rank among their neighbours.
-  __device__ void c4_blocked_attach(int32_t th) {
+  __device__ void c4_blocked_attach() {
     const int64_t bn = P().b_n, bE = P().b_E;
     const int32_t r0 = P().r0;
     lbs_for_each(B.b_e, bn, bE, lbs_ws(), [&](const Lbs& L) {
@@ -829,7 +933,7 @@ struct K {
             if (hw < 0 && ~hw >= r0 && lo_of(x) == kCenter) atomicMin(B.pull + L.item(i), ~hw);
           }
         }
-        attach_one(push, u, r, x, th);
+        attach_one(push, u, r, x);
       }
     });
     append_flush(app_buf(), new_list());
@@ -865,7 +969,7 @@ struct K {
 
   // ---------------- removal: residual degrees and the objective --------------
   // ---------------- removal: residual degrees and the objective --------------
-  __device__ void decrement(int32_t th) {
+  __device__ void decrement() {
     const int64_t nn = P().new_n, nE = P().new_E;
     lbs_for_each(B.new_e, nn, nE, lbs_ws(), [&](const Lbs& L) {
       int32_t u[kLbsK], w[kLbsK], lu[kLbsK];
@@ -889,10 +993,7 @@ struct K {
         if (!L.ok(q)) continue;
         const int32_t hw = hi_of(x[q]);
         if (hw == kAliveHi) {
-          const uint32_t d = atomicSub(reinterpret_cast<unsigned*>(B.st + w[q]), 1u);   // low word
-          if (d == 0) { fail(kErrInternal); continue; }
-          hist_add(th, d, -1);
-          hist_add(th, d - 1, 1);
+          atomicSub(reinterpret_cast<unsigned*>(B.st + w[q]), 1u);   // low word, result unused
         } else if (decode_label(hw) == lu[q]) {
           if (hw < 0) t.mc += 1; else t.mm += 1;
         }
@@ -920,7 +1021,6 @@ __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared& S = *reinterpret_cast<Shared*>(smem_raw);
   K k{B, B.ctl, &S, gridDim.x, 0u, Tally{0, 0, 0, 0, 0, 0, 0}};
-  for (int i = threadIdx.x; i < kHist; i += blockDim.x) S.hist[i] = 0;
   if ((threadIdx.x & 31) == 0) S.app[threadIdx.x >> 5].n = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = 0; i < 8; ++i) S.co.ph_ns[i] = 0;
@@ -937,19 +1037,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ 
       if (!k.rebuild()) goto out;
       continue;
     }
+    if (S.plan.state == kRebuildDelta) {
+      if (!k.delta_rebuild()) goto out;
+      continue;
+    }
+    if (S.plan.state == kScanH) {
+      if (!k.heavy_scan()) goto out;
+      continue;
+    }
     if (!k.select(algo)) goto out;
     {
-      const int32_t th = S.plan.th;
       if (algo == kAlgoCW) {
-        k.attach_from_actives(false, th);
-        k.hist_flush(th);
+        k.attach_from_actives(false);
         if (!k.sync(4, [&] { k.co_lists_ready(); })) goto out;
       } else {
         k.c4_detect();
         if (!k.sync(4)) goto out;
         k.c4_classify();
-        k.attach_from_actives(true, th);
-        k.hist_flush(th);
+        k.attach_from_actives(true);
         if (!k.sync(4, [&] {
               if (threadIdx.x == 0) {
                 const unsigned long long pk = vload(&C->blk_pack);
@@ -985,17 +1090,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ 
                 }))
               goto out;
           }
-          k.c4_blocked_attach(th);
-          k.hist_flush(th);
+          k.c4_blocked_attach();
           if (!k.sync(5)) goto out;
           k.c4_pull_finalize();
           if (!k.sync(5, [&] { k.co_lists_ready(); })) goto out;
         }
       }
-      k.decrement(th);
-      k.hist_flush(th);
+      k.decrement();
       k.flush_round_tallies();
-      if (!k.sync(6, [&] { k.co_end_round(); k.rebuild_plan_fields(); })) goto out;
+      if (!k.sync(6, [&] { k.co_end_round(); })) goto out;
     }
   }
 out:
@@ -1048,7 +1151,7 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   b += 2 * align_up(4 * nn) + 2 * align_up(8 * nn);   // act_v, act_r, act_e, act_d
   b += align_up(4 * nn) + 2 * align_up(8 * nn);       // new_v, new_e, new_d
   b += align_up(4 * nn);                 // size
-  b += align_up(4 * ((size_t)max_deg + 2 + kHist));   // cnt
+  b += 3 * align_up(4 * nn);             // hv, nz0, nz1
   b += 3 * align_up(nn);                 // blk_flag, hit_c, hit_p
   b += align_up(4 * nn);                 // pull
   b += align_up(4 * nn) + 2 * align_up(8 * nn);       // b_j, b_e, b_d
@@ -1072,7 +1175,9 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   B->new_e = reinterpret_cast<int64_t*>(take(8 * nn));
   B->new_d = reinterpret_cast<int64_t*>(take(8 * nn));
   B->size = reinterpret_cast<int32_t*>(take(4 * nn));
-  B->cnt = reinterpret_cast<int32_t*>(take(4 * ((size_t)max_deg + 2 + kHist)));
+  B->hv = reinterpret_cast<int32_t*>(take(4 * nn));
+  B->nz0 = reinterpret_cast<int32_t*>(take(4 * nn));
+  B->nz1 = reinterpret_cast<int32_t*>(take(4 * nn));
   B->blk_flag = reinterpret_cast<uint8_t*>(take(nn));
   B->hit_c = reinterpret_cast<uint8_t*>(take(nn));
   B->hit_p = reinterpret_cast<uint8_t*>(take(nn));
