@@ -327,14 +327,12 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
   CC_TRY(launch_rounds(b, algo, ppm, g->grid, s));
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[2], s));
   const bool dev = is_device_ptr(labels_out);
-  if (labels_out) {
-    if (dev) {
-      CC_TRY(launch_finalize_labels(b, labels_out, s));
-    } else {
-      if ((rc = ensure_labels_tmp(g)) != CC_OK) return rc;
-      CC_TRY(launch_finalize_labels(b, g->labels_tmp, s));
-      CC_TRY(cudaMemcpyAsync(labels_out, g->labels_tmp, 4 * (size_t)g->n, cudaMemcpyDeviceToHost, s));
-    }
+  if (labels_out && !dev) {
+    if ((rc = ensure_labels_tmp(g)) != CC_OK) return rc;
+    CC_TRY(launch_finalize_labels(b, g->labels_tmp, s));
+    CC_TRY(cudaMemcpyAsync(labels_out, g->labels_tmp, 4 * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+  } else {
+    CC_TRY(launch_finalize_labels(b, labels_out, s));   // also the objective's pair term
   }
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[3], s));
   CC_TRY(cudaMemcpyAsync(g->ctl_host, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));

@@ -211,6 +211,8 @@ constexpr int kLbsBatches = 8;
 struct LbsWarp {
   int32_t mark[kLbsW];   // relative item index per position
   int32_t rel[kLbsW];    // item start relative to the batch base
+  int64_t dlt[kLbsW];    // per-item CSR delta (prefetched when given)
+  int32_t vtx[kLbsW];    // per-item vertex or payload (prefetched when given)
   int32_t next;          // relative index of the item starting the next batch
   int32_t pad;
 };
@@ -228,6 +230,9 @@ struct Lbs {
   __device__ __forceinline__ int64_t in_row(int t) const {
     return (int64_t)((threadIdx.x & 31) + 32 * t) - ws->rel[ri[t]];
   }
+  // prefetched per-item data (only when the walk was given the arrays)
+  __device__ __forceinline__ int64_t csr(int t) const { return edge(t) + ws->dlt[ri[t]]; }
+  __device__ __forceinline__ int32_t vtx(int t) const { return ws->vtx[ri[t]]; }
 };
 
 // Number of elements of the sorted array a[0..n) that are <= x, by a 33-ary
@@ -252,7 +257,8 @@ __device__ __forceinline__ int64_t warp_upper_bound(const int64_t* a, int64_t n,
 
 template <class F>
 __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems, int64_t E, LbsWarp* ws,
-                                             F&& f) {
+                                             F&& f, const int64_t* delta = nullptr,
+                                             const int32_t* vtx = nullptr) {
   if (E <= 0) return;
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -270,7 +276,11 @@ __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems
 #pragma unroll
       for (int t = 0; t < kLbsK; ++t) {
         const int64_t jj = j0 + lane + 32 * t;
-        s[t] = jj < nitems ? ldcg(epos + jj) : INT64_MAX;
+        const bool in = jj < nitems;
+        s[t] = in ? ldcg(epos + jj) : INT64_MAX;
+        // per-item data loads issue together with the start offsets
+        if (delta) ws->dlt[lane + 32 * t] = in ? ldcg(delta + jj) : 0;
+        if (vtx) ws->vtx[lane + 32 * t] = in ? ldcg(vtx + jj) : 0;
         ws->mark[lane + 32 * t] = -1;
       }
       if (lane == 0) ws->next = -1;

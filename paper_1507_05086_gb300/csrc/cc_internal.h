@@ -106,7 +106,8 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
 // Largest co-resident grid for the persistent round kernel on this device.
 int rounds_grid_size(int device);
 cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, int grid, cudaStream_t stream);
-// labels_out[v] = center vertex id (order[center rank]).
+// labels_out[v] = center vertex id (order[center rank]) when labels_out is
+// not null; always adds the pair term sum_c C(s_c, 2) to ctl->pairs.
 cudaError_t launch_finalize_labels(const RoundBuffers& b, int32_t* labels_out, cudaStream_t stream);
 
 // ---- objective and validation (cc_objective.cu) ------------------------------

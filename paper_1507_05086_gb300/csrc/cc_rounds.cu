@@ -95,7 +95,6 @@ struct Shared {
 struct Tally {
   int32_t centers, attached, noncenter, blocked;
   uint32_t mc, mm;              // member-center and member-member edges
-  unsigned long long pairs;     // growth of sum_c C(s_c, 2)
 };
 
 struct K {
@@ -177,20 +176,6 @@ struct K {
   __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, nullptr, &C->blk_pack}; }
   __device__ LbsWarp* lbs_ws() const { return &S->lbs[threadIdx.x >> 5]; }
   __device__ AppendBuf* app_buf() const { return &S->app[threadIdx.x >> 5]; }
-
-  // Pair tally of cluster growth: a member joining the cluster of center rank
-  // c adds (current size) new pairs, sum_c C(s_c, 2) in total.  Lanes with the
-  // same c share one atomic.
-  __device__ void add_member(bool want, int32_t c) {
-    const int lane = threadIdx.x & 31;
-    const int key = want ? c : -1;
-    const unsigned grp = __match_any_sync(FULL, key);
-    const int leader = __ffs(grp) - 1;
-    int old = 0;
-    if (want && lane == leader) old = atomicAdd(B.size + c, __popc(grp));
-    old = __shfl_sync(FULL, old, leader);
-    if (want) t.pairs += 1ull + (unsigned long long)(old + __popc(grp & ((1u << lane) - 1u)));
-  }
 
   // Entry i of the current alive list: (rank, vertex).  Before the first
   // compaction the list is implicit: entry i is (i, order[i]).
@@ -773,8 +758,10 @@ struct K {
     // degree 1: nothing to decrement, and no other center can reach it, so
     // its label is already final.
     const bool single = fresh && d_old == 1;
-    if (single) t.mc += 1;
-    add_member(single, r);
+    if (single) {
+      t.mc += 1;
+      atomicAdd(B.size + r, 1);          // one more member (result unused)
+    }
     const bool want = fresh && d_old != 1;
     int64_t row = 0;
     int32_t len = 0;
@@ -789,22 +776,18 @@ struct K {
     const int64_t an = P().act_n, aE = P().act_E;
     lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
       bool push[kLbsK];
-      int32_t r[kLbsK], u[kLbsK];
-      int64_t pos[kLbsK];
+      int32_t u[kLbsK];
       unsigned long long x[kLbsK];
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         push[q] = L.ok(q) && (!skip_blocked || ldcg(B.blk_flag + L.item(q)) == 0);
-        r[q] = push[q] ? ldcg(B.act_r + L.item(q)) : 0;
-        pos[q] = push[q] ? L.edge(q) + ldcg(B.act_d + L.item(q)) : 0;
+        u[q] = push[q] ? __ldg(B.col + L.csr(q)) : 0;
       }
-#pragma unroll
-      for (int q = 0; q < kLbsK; ++q) u[q] = push[q] ? __ldg(B.col + pos[q]) : 0;
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) x[q] = push[q] ? ldcg(B.st + u[q]) : 0;
 #pragma unroll
-      for (int q = 0; q < kLbsK; ++q) attach_one(push[q], u[q], r[q], x[q]);
-    });
+      for (int q = 0; q < kLbsK; ++q) attach_one(push[q], u[q], L.vtx(q), x[q]);
+    }, B.act_d, B.act_r);
     append_flush(app_buf(), new_list());
   }
 
@@ -813,23 +796,17 @@ struct K {
     const int64_t an = P().act_n, aE = P().act_E;
     const int32_t r0 = P().r0;
     lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
-      int32_t rv[kLbsK], u[kLbsK];
-      int64_t pos[kLbsK];
+      int32_t u[kLbsK];
 #pragma unroll
-      for (int q = 0; q < kLbsK; ++q) {
-        rv[q] = L.ok(q) ? ldcg(B.act_r + L.item(q)) : 0;
-        pos[q] = L.ok(q) ? L.edge(q) + ldcg(B.act_d + L.item(q)) : 0;
-      }
-#pragma unroll
-      for (int q = 0; q < kLbsK; ++q) u[q] = L.ok(q) ? __ldg(B.col + pos[q]) : 0;
+      for (int q = 0; q < kLbsK; ++q) u[q] = L.ok(q) ? __ldg(B.col + L.csr(q)) : 0;
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         if (!L.ok(q)) continue;
         const int32_t hw = hi_of(ldcg(B.st + u[q]));
         // an earlier active neighbour: v must wait (isCenter)
-        if (hw < 0 && ~hw >= r0 && ~hw < rv[q]) B.blk_flag[L.item(q)] = 1;
+        if (hw < 0 && ~hw >= r0 && ~hw < L.vtx(q)) B.blk_flag[L.item(q)] = 1;
       }
-    });
+    }, B.act_d, B.act_r);
   }
 
   // C4: unblocked actives become centers; blocked ones go to the blocked list.
@@ -972,25 +949,19 @@ struct K {
   __device__ void decrement() {
     const int64_t nn = P().new_n, nE = P().new_E;
     lbs_for_each(B.new_e, nn, nE, lbs_ws(), [&](const Lbs& L) {
-      int32_t u[kLbsK], w[kLbsK], lu[kLbsK];
-      int64_t pos[kLbsK];
+      int32_t w[kLbsK], lu[kLbsK];
       unsigned long long x[kLbsK];
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
-        u[q] = L.ok(q) ? ldcg(B.new_v + L.item(q)) : 0;
-        pos[q] = L.ok(q) ? L.edge(q) + ldcg(B.new_d + L.item(q)) : 0;
+        w[q] = L.ok(q) ? __ldg(B.col + L.csr(q)) : 0;
+        lu[q] = L.ok(q) ? hi_of(ldcg(B.st + L.vtx(q))) : 0;
       }
 #pragma unroll
-      for (int q = 0; q < kLbsK; ++q) w[q] = L.ok(q) ? __ldg(B.col + pos[q]) : 0;
+      for (int q = 0; q < kLbsK; ++q) x[q] = L.ok(q) ? ldcg(B.st + w[q]) : 0;
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
-        lu[q] = L.ok(q) ? hi_of(ldcg(B.st + u[q])) : 0;
-        x[q] = L.ok(q) ? ldcg(B.st + w[q]) : 0;
-      }
-#pragma unroll
-      for (int q = 0; q < kLbsK; ++q) {
-        add_member(L.ok(q) && L.in_row(q) == 0, lu[q]);   // once per removed member
         if (!L.ok(q)) continue;
+        if (L.in_row(q) == 0) atomicAdd(B.size + lu[q], 1);   // once per removed member
         const int32_t hw = hi_of(x[q]);
         if (hw == kAliveHi) {
           atomicSub(reinterpret_cast<unsigned*>(B.st + w[q]), 1u);   // low word, result unused
@@ -998,7 +969,7 @@ struct K {
           if (hw < 0) t.mc += 1; else t.mm += 1;
         }
       }
-    });
+    }, B.new_d, B.new_v);
   }
 
   // Reduce the round tallies of this block into the control block.
@@ -1011,16 +982,14 @@ struct K {
       const long long s = block_sum<int64_t>(v[i], S->scr);
       if (threadIdx.x == 0 && s != 0) atomicAdd(reinterpret_cast<unsigned long long*>(dst[i]), (unsigned long long)s);
     }
-    const unsigned long long pr = (unsigned long long)block_sum<int64_t>((int64_t)t.pairs, S->scr);
-    if (threadIdx.x == 0 && pr != 0) atomicAdd(&C->pairs, pr);
-    t = Tally{0, 0, 0, 0, 0, 0, 0};
+    t = Tally{0, 0, 0, 0, 0, 0};
   }
 };
 
 __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ RoundBuffers B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared& S = *reinterpret_cast<Shared*>(smem_raw);
-  K k{B, B.ctl, &S, gridDim.x, 0u, Tally{0, 0, 0, 0, 0, 0, 0}};
+  K k{B, B.ctl, &S, gridDim.x, 0u, Tally{0, 0, 0, 0, 0, 0}};
   if ((threadIdx.x & 31) == 0) S.app[threadIdx.x >> 5].n = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     for (int i = 0; i < 8; ++i) S.co.ph_ns[i] = 0;
@@ -1126,18 +1095,30 @@ __global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm) {
   }
 }
 
+// Labels (center vertex id = order[center rank]) and the pair term of the
+// objective: vertex v is the center of cluster c exactly when order[c] == v,
+// and its cluster has 1 + size[c] vertices.
 __global__ void k_finalize_labels(RoundBuffers B, int32_t* __restrict__ labels) {
+  __shared__ int64_t scr[33];
   const int64_t n = B.n;
+  unsigned long long pairs = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int32_t hw = hi_of(B.st[v]);
     const int32_t c = decode_label(hw);
     if (hw == kAliveHi || c < 0 || c >= n) {
       atomicCAS(&B.ctl->err, kOk, kErrInternal);
-      labels[v] = -1;
-    } else {
-      labels[v] = __ldg(B.order + c);
+      if (labels) labels[v] = -1;
+      continue;
+    }
+    const int32_t cv = __ldg(B.order + c);
+    if (labels) labels[v] = cv;
+    if (cv == v) {
+      const unsigned long long sz = 1ull + (unsigned long long)B.size[c];
+      pairs += sz * (sz - 1) / 2;
     }
   }
+  pairs = (unsigned long long)block_sum<int64_t>((int64_t)pairs, scr);
+  if (threadIdx.x == 0 && pairs) atomicAdd(&B.ctl->pairs, pairs);
 }
 
 }  // namespace
@@ -1217,7 +1198,7 @@ cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, int 
 cudaError_t launch_finalize_labels(const RoundBuffers& b, int32_t* labels_out, cudaStream_t stream) {
   if (b.n <= 0) return cudaSuccess;
   const int64_t want = (b.n + 255) / 256;
-  const int grid = (int)(want < 4096 ? want : 4096);
+  const int grid = (int)(want < 2048 ? want : 2048);
   k_finalize_labels<<<grid, 256, 0, stream>>>(b, labels_out);
   return cudaGetLastError();
 }
