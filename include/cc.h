@@ -180,6 +180,30 @@ int cc_last_timings(const cc_graph* g, float* ms_out);
  */
 int cc_last_phase_times(const cc_graph* g, double* ms_out, int32_t cap);
 
+/*
+ * cc_disagreements_static -- the same objective as cc_disagreements, for
+ * callers that cannot allocate memory when they need it: code running inside
+ * a fixed memory pool or arena, or under a "no allocation after start-up"
+ * rule.  It allocates nothing: besides the caller's buffers it uses one
+ * scratch area compiled into the library (about 4 MB per GPU, reserved when
+ * the library is loaded on that GPU and held until the process exits).  The
+ * paper has no counterpart; this is a deployment variant.
+ *   n            number of vertices, 0 <= n <= CC_STATIC_MAX_N (larger n:
+ *                CC_ERR_INVALID_ARG).
+ *   row_offsets  device int64[n+1], col_idx device int32[off[n]]: a CSR as
+ *                cc_graph_create accepts it (not validated here).
+ *   labels       device int32[n], values in [0, n).
+ *   out          device int64: receives D, or -1 if a label is out of range.
+ *   cuda_stream  stream for the work; the call returns without waiting.
+ * Every call shares the one scratch area: calls whose work overlaps on the GPU
+ * race and must be ordered by the caller.  The first call on a device looks
+ * up the scratch address (cudaGetSymbolAddress); make it before any stream
+ * capture starts.
+ */
+#define CC_STATIC_MAX_N (1 << 20)
+int cc_disagreements_static(int64_t n, const int64_t* row_offsets, const int32_t* col_idx,
+                            const int32_t* labels, int64_t* out, void* cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char* cc_status_string(int status);
 

@@ -84,6 +84,8 @@ def load(build_if_missing: bool = True):
         lib.cc_last_timings.argtypes = [vp, vp]
         lib.cc_last_phase_times.restype = ci
         lib.cc_last_phase_times.argtypes = [vp, vp, i32]
+        lib.cc_disagreements_static.restype = ci
+        lib.cc_disagreements_static.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.cc_batch_run.restype = ci
         lib.cc_batch_run.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp, vp, vp]
         _lib = lib
