@@ -161,6 +161,18 @@ int cc_batch_run(cc_graph* const* gs, int32_t count, int algo, double eps,
                  int32_t* best_j, int64_t* best_D, int32_t* rounds);
 
 /*
+ * cc_batch_jobs -- the jobs of cc_batch_run without the best-of-k reduction:
+ * D_out[i * k_perms + j] and rounds_out[i * k_perms + j] (host arrays, either
+ * may be NULL) for graph i under seed seeds[i] + j.  Small graphs run one per
+ * thread block, medium graphs one per team of blocks, all in one launch per
+ * size class; graphs above 2^21 vertices run on the whole GPU one at a time.
+ * All graphs must live on the same device.
+ */
+int cc_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps,
+                  const uint64_t* seeds, int32_t k_perms, int64_t* D_out,
+                  int32_t* rounds_out);
+
+/*
  * Kernel timing hook.  cc_graph_set_timing(g, 1) makes later cc_cluster /
  * cc_cluster_ex calls on g record CUDA events on the graph's stream around
  * their three device stages; cc_last_timings then writes the durations in

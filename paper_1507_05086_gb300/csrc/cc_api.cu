@@ -4,13 +4,23 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <algorithm>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "../../include/cc.h"
 #include "cc_internal.h"
 
 using namespace ccg;
+
+namespace {
+// batched size classes: up to kBatchSmallN vertices one block runs a job, up
+// to kBatchTeamN a team of kBatchTeamBlocks blocks, beyond that the whole grid
+constexpr int64_t kBatchSmallN = 1 << 16;
+constexpr int64_t kBatchTeamN = 1 << 21;
+constexpr int kBatchTeamBlocks = 8;
+}  // namespace
 
 struct cc_graph {
   int device = 0;
@@ -416,30 +426,134 @@ int cc_disagreements(cc_graph* g, const int32_t* labels, int64_t* out) {
   return CC_OK;
 }
 
-int cc_batch_run(cc_graph* const* gs, int32_t count, int algo, double eps, const uint64_t* seeds, int32_t k_perms,
-                 int32_t* const* labels_out, int32_t* best_j, int64_t* best_D, int32_t* rounds) {
+}  // extern "C"
+
+namespace {
+
+// Runs every (graph, permutation) job; jobs[i * k_perms + j] gets its rounds
+// and disagreements.
+int run_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, const uint64_t* seeds, int32_t k_perms,
+                   std::vector<BatchJob>& jobs) {
   if (count < 0 || k_perms < 1 || (count > 0 && (!gs || !seeds))) return CC_ERR_INVALID_ARG;
+  if (algo != CC_ALGO_C4 && algo != CC_ALGO_CLUSTERWILD) return CC_ERR_INVALID_ARG;
   int64_t ppm = 0;
   int rc = eps_ppm_of(eps, &ppm);
   if (rc != CC_OK) return rc;
-  for (int32_t i = 0; i < count; ++i) {
-    if (!gs[i]) return CC_ERR_INVALID_ARG;
-    int64_t bestd = INT64_MAX;
-    int32_t bj = -1, br = 0;
+  if (count == 0) { jobs.clear(); return CC_OK; }
+  for (int32_t i = 0; i < count; ++i)
+    if (!gs[i] || gs[i]->device != gs[0]->device) return CC_ERR_INVALID_ARG;
+  cudaSetDevice(gs[0]->device);
+  cudaStream_t s = gs[0]->stream;
+  for (int32_t i = 1; i < count; ++i)
+    if (gs[i]->stream != s) CC_TRY(cudaStreamSynchronize(gs[i]->stream));
+  // one job per (graph, permutation)
+  const int64_t njobs = (int64_t)count * k_perms;
+  jobs.assign((size_t)njobs, BatchJob{});
+  for (int32_t i = 0; i < count; ++i)
     for (int32_t j = 0; j < k_perms; ++j) {
-      int32_t r = 0;
-      int64_t d = 0;
-      rc = cc_cluster(gs[i], algo, eps, seeds[i] + (uint64_t)j, nullptr, &r, &d);
-      if (rc != CC_OK) return rc;
-      if (d < bestd) { bestd = d; bj = j; br = r; }
+      BatchJob& jb = jobs[(size_t)i * k_perms + j];
+      const cc_graph* g = gs[i];
+      jb = BatchJob{};
+      jb.off = g->off; jb.col = g->col; jb.nz = g->nz_row; jb.nz_n = g->nz_n;
+      jb.n = g->n; jb.nnz = g->nnz; jb.max_deg = g->max_deg;
+      jb.seed = seeds[i] + (uint64_t)j;
+      jb.err = 1;
+      jb.rounds = 0;
+      jb.D = 0;
     }
-    if (labels_out && labels_out[i]) {
-      rc = cc_cluster(gs[i], algo, eps, seeds[i] + (uint64_t)bj, labels_out[i], nullptr, nullptr);
-      if (rc != CC_OK) return rc;
+  // size classes: one block per job, eight-block teams, or the whole grid
+  std::vector<int64_t> cls[3];
+  for (int64_t q = 0; q < njobs; ++q) {
+    const int64_t n = jobs[(size_t)q].n;
+    cls[n <= kBatchSmallN ? 0 : (n <= kBatchTeamN ? 1 : 2)].push_back(q);
+  }
+  const int grid0 = batch_grid_size(gs[0]->device);
+  for (int c = 0; c < 2; ++c) {
+    std::vector<int64_t>& ids = cls[c];
+    if (ids.empty()) continue;
+    std::sort(ids.begin(), ids.end(), [&](int64_t a, int64_t b2) { return jobs[(size_t)a].n > jobs[(size_t)b2].n; });
+    const int team = c == 0 ? 1 : kBatchTeamBlocks;
+    const int teams = grid0 / team;
+    if (teams < 1) return CC_ERR_INTERNAL;
+    const int grid = teams * team;
+    const int64_t n_max = jobs[(size_t)ids[0]].n;
+    const size_t slot = align_up(batch_slot_bytes(n_max, team));
+    void* ws = nullptr;
+    CC_TRY(dalloc(&ws, slot * (size_t)teams, s));
+    std::vector<RoundBuffers> slots((size_t)teams);
+    for (int t = 0; t < teams; ++t) {
+      batch_slot_carve(static_cast<char*>(ws) + slot * (size_t)t, n_max, team, &slots[(size_t)t]);
+      CC_TRY(cudaMemsetAsync(slots[(size_t)t].ctl, 0, sizeof(Ctl), s));
     }
+    std::vector<BatchJob> sub(ids.size());
+    for (size_t q = 0; q < ids.size(); ++q) sub[q] = jobs[(size_t)ids[q]];
+    BatchJob* jobs_dev = nullptr;
+    RoundBuffers* slots_dev = nullptr;
+    CC_TRY(dalloc(&jobs_dev, sizeof(BatchJob) * sub.size(), s));
+    CC_TRY(dalloc(&slots_dev, sizeof(RoundBuffers) * slots.size(), s));
+    CC_TRY(cudaMemcpyAsync(jobs_dev, sub.data(), sizeof(BatchJob) * sub.size(), cudaMemcpyHostToDevice, s));
+    CC_TRY(cudaMemcpyAsync(slots_dev, slots.data(), sizeof(RoundBuffers) * slots.size(), cudaMemcpyHostToDevice, s));
+    CC_TRY(launch_batch(jobs_dev, (int)sub.size(), slots_dev, team, grid, algo, ppm, s));
+    CC_TRY(cudaMemcpyAsync(sub.data(), jobs_dev, sizeof(BatchJob) * sub.size(), cudaMemcpyDeviceToHost, s));
+    dfree(jobs_dev, s);
+    dfree(slots_dev, s);
+    dfree(ws, s);
+    CC_TRY(cudaStreamSynchronize(s));
+    for (size_t q = 0; q < ids.size(); ++q) {
+      if (sub[q].err != 0) return sub[q].err == CC_ERR_TIMEOUT ? CC_ERR_TIMEOUT : CC_ERR_INTERNAL;
+      jobs[(size_t)ids[q]].rounds = sub[q].rounds;
+      jobs[(size_t)ids[q]].D = sub[q].D;
+      jobs[(size_t)ids[q]].err = 0;
+    }
+  }
+  for (int64_t q : cls[2]) {   // graphs too large for a team: the whole grid per job
+    BatchJob& jb = jobs[(size_t)q];
+    int32_t r = 0;
+    int64_t d = 0;
+    rc = cc_cluster(gs[q / k_perms], algo, eps, jb.seed, nullptr, &r, &d);
+    if (rc != CC_OK) return rc;
+    jb.rounds = r;
+    jb.D = d;
+    jb.err = 0;
+  }
+  return CC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int cc_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, const uint64_t* seeds, int32_t k_perms,
+                  int64_t* D_out, int32_t* rounds_out) {
+  std::vector<BatchJob> jobs;
+  const int rc = run_batch_jobs(gs, count, algo, eps, seeds, k_perms, jobs);
+  if (rc != CC_OK) return rc;
+  for (size_t q = 0; q < jobs.size(); ++q) {
+    if (D_out) D_out[q] = jobs[q].D;
+    if (rounds_out) rounds_out[q] = (int32_t)jobs[q].rounds;
+  }
+  return CC_OK;
+}
+
+int cc_batch_run(cc_graph* const* gs, int32_t count, int algo, double eps, const uint64_t* seeds, int32_t k_perms,
+                 int32_t* const* labels_out, int32_t* best_j, int64_t* best_D, int32_t* rounds) {
+  std::vector<BatchJob> jobs;
+  int rc = run_batch_jobs(gs, count, algo, eps, seeds, k_perms, jobs);
+  if (rc != CC_OK) return rc;
+  // best of k per graph: lowest D, ties to the lowest j
+  for (int32_t i = 0; i < count; ++i) {
+    int32_t bj = 0;
+    for (int32_t j = 1; j < k_perms; ++j)
+      if (jobs[(size_t)i * k_perms + j].D < jobs[(size_t)i * k_perms + bj].D) bj = j;
+    const BatchJob& b = jobs[(size_t)i * k_perms + bj];
     if (best_j) best_j[i] = bj;
-    if (best_D) best_D[i] = bestd;
-    if (rounds) rounds[i] = br;
+    if (best_D) best_D[i] = b.D;
+    if (rounds) rounds[i] = (int32_t)b.rounds;
+    if (labels_out && labels_out[i]) {
+      // labels of the winning permutation (the same deterministic clustering)
+      rc = cc_cluster(gs[i], algo, eps, b.seed, labels_out[i], nullptr, nullptr);
+      if (rc != CC_OK) return rc;
+    }
   }
   return CC_OK;
 }

@@ -255,14 +255,14 @@ __device__ __forceinline__ int64_t warp_upper_bound(const int64_t* a, int64_t n,
   return lo + __popc(__ballot_sync(FULL, le));
 }
 
+// gwarp / nwarps: this warp's index among, and the number of, the warps that
+// share the walk (the whole grid, or one team of blocks).
 template <class F>
-__device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems, int64_t E, LbsWarp* ws,
-                                             F&& f, const int64_t* delta = nullptr,
-                                             const int32_t* vtx = nullptr) {
+__device__ __forceinline__ void lbs_for_each_in(int64_t gwarp, int64_t nwarps, const int64_t* epos, int64_t nitems,
+                                                int64_t E, LbsWarp* ws, F&& f, const int64_t* delta = nullptr,
+                                                const int32_t* vtx = nullptr) {
   if (E <= 0) return;
   const int lane = threadIdx.x & 31;
-  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   // up to kLbsBatches batches per chunk, fewer when the list is short, so
   // that short lists still spread over many warps
   int64_t nb = E / (nwarps * (int64_t)kLbsW * 2);
@@ -344,6 +344,13 @@ __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems
       else j0 += last;
     }
   }
+}
+
+template <class F>
+__device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems, int64_t E, LbsWarp* ws, F&& f,
+                                             const int64_t* delta = nullptr, const int32_t* vtx = nullptr) {
+  lbs_for_each_in(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5,
+                  epos, nitems, E, ws, f, delta, vtx);
 }
 
 // Lists of adjacency rows.  A list counter packs (items << 33 | edges): one

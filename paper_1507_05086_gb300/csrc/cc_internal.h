@@ -98,7 +98,33 @@ struct RoundBuffers {
   RoundStat* stats;
   int64_t stats_cap;
   Ctl* ctl;
+  // batched jobs only: writable order, permutation scratch
+  int32_t* order_w;
+  int32_t* ptmp;
+  int64_t* pcnt;
 };
+
+// One job of a batched launch: a graph and a permutation seed, plus results.
+struct BatchJob {
+  const int64_t* off;
+  const int32_t* col;
+  const int32_t* nz;
+  int64_t nz_n;
+  int64_t n, nnz;
+  int32_t max_deg;
+  int32_t err;          // result: device status (0 = ok, 1 = not run)
+  uint64_t seed;
+  int64_t rounds;       // result
+  int64_t D;            // result: disagreements
+};
+
+// Largest co-resident grid of the batched kernel on this device.
+int batch_grid_size(int device);
+// Per-team scratch of a batched launch, sized for the largest job of the launch.
+size_t batch_slot_bytes(int64_t n_max, int team_size);
+void batch_slot_carve(void* ws, int64_t n_max, int team_size, RoundBuffers* B);
+cudaError_t launch_batch(const BatchJob* jobs_dev, int njobs, const RoundBuffers* slots_dev, int team_size,
+                         int grid, int algo, int64_t eps_ppm, cudaStream_t stream);
 
 size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid);
 // Carve a workspace of rounds_workspace_bytes() into RoundBuffers (pointers only).

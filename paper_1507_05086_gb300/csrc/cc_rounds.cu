@@ -80,6 +80,21 @@ struct Coord {
 };
 
 // Shared memory of one block (dynamic: larger than the 48 KB static limit).
+// Bucket-sort scratch of the in-kernel permutation (batched jobs).
+constexpr int kPermCap = 1536;        // vertices per bucket sorted in shared memory
+constexpr int kPermSubBits = 10;
+constexpr int kPermSub = 1 << kPermSubBits;
+constexpr int kPermMaxBuckets = 4096;
+
+struct PermSmem {
+  uint64_t sk[kPermCap];
+  uint64_t ok[kPermCap];
+  int32_t sv[kPermCap];
+  int32_t ov[kPermCap];
+  int32_t cnt[kPermSub + 1];
+  int32_t hist[kPermMaxBuckets];
+};
+
 struct Shared {
   Plan plan;
   Coord co;
@@ -87,8 +102,13 @@ struct Shared {
   int dec;
   int64_t scr[33];
   int64_t bcast[8];
-  LbsWarp lbs[kWarps];
-  AppendBuf app[kWarps];
+  union {
+    struct {
+      LbsWarp lbs[kWarps];
+      AppendBuf app[kWarps];
+    } w;
+    PermSmem perm;
+  } u;
 };
 
 // Per-thread tallies of one round (flushed at every round end).
@@ -97,13 +117,23 @@ struct Tally {
   uint32_t mc, mm;              // member-center and member-member edges
 };
 
+// The blocks that run one clustering job: the whole grid, or a team of
+// G blocks inside a batched launch (bid = this block's rank in the team).
 struct K {
   const RoundBuffers& B;
   Ctl* C;
   Shared* S;
   unsigned G;
+  unsigned bid;
   unsigned epoch;
   Tally t;
+
+  template <class F>
+  __device__ __forceinline__ void lbs(const int64_t* epos, int64_t nitems, int64_t E, F&& f,
+                                      const int64_t* delta = nullptr, const int32_t* vtx = nullptr) {
+    lbs_for_each_in(((int64_t)bid * blockDim.x + threadIdx.x) >> 5, ((int64_t)G * blockDim.x) >> 5, epos, nitems,
+                    E, lbs_ws(), f, delta, vtx);
+  }
 
   __device__ __forceinline__ const Plan& P() const { return S->plan; }
   __device__ __forceinline__ Coord& co() const { return S->co; }
@@ -119,8 +149,21 @@ struct K {
   __device__ bool sync(int cat, A&& act) {
     __syncthreads();
     ++epoch;
+    if (G == 1) {                       // a one-block team is its own coordinator
+      if (threadIdx.x == 0) {
+        const unsigned long long now = globaltimer_ns();
+        S->co.ph_ns[cat] += now - S->co.t0;
+        S->co.t0 = now;
+      }
+      __syncthreads();
+      if (ld_volatile_int(&C->err) == kOk) act();
+      __syncthreads();
+      if (threadIdx.x == 0 && ld_volatile_int(&C->err) != kOk) S->plan.state = kAbort;
+      __syncthreads();
+      return S->plan.state != kAbort;
+    }
     if (threadIdx.x == 0) atom_add_release(&C->arrive, 1u);
-    if (blockIdx.x == 0) {
+    if (bid == 0) {
       if (threadIdx.x == 0) {
         const unsigned target = G * epoch;
         const uint64_t t0 = globaltimer_ns();
@@ -174,8 +217,8 @@ struct K {
 
   __device__ RowList new_list() const { return RowList{B.new_v, B.new_e, B.new_d, nullptr, &C->new_pack}; }
   __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, nullptr, &C->blk_pack}; }
-  __device__ LbsWarp* lbs_ws() const { return &S->lbs[threadIdx.x >> 5]; }
-  __device__ AppendBuf* app_buf() const { return &S->app[threadIdx.x >> 5]; }
+  __device__ LbsWarp* lbs_ws() const { return &S->u.w.lbs[threadIdx.x >> 5]; }
+  __device__ AppendBuf* app_buf() const { return &S->u.w.app[threadIdx.x >> 5]; }
 
   // Entry i of the current alive list: (rank, vertex).  Before the first
   // compaction the list is implicit: entry i is (i, order[i]).
@@ -187,7 +230,7 @@ struct K {
   // contiguous slice of [lo, lo+len) for this block
   __device__ void slice(int64_t lo, int64_t len, int64_t* s, int64_t* e) const {
     const int64_t chunk = (len + G - 1) / G;
-    *s = lo + chunk * blockIdx.x;
+    *s = lo + chunk * bid;
     *e = *s + chunk < lo + len ? *s + chunk : lo + len;
     if (*s > *e) *s = *e;
   }
@@ -390,7 +433,7 @@ struct K {
         cnt += (a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi) ? 1 : 0;
     }
     cnt = block_sum<int64_t>(cnt, S->scr);
-    if (threadIdx.x == 0) B.blk_a[blockIdx.x] = cnt;
+    if (threadIdx.x == 0) B.blk_a[bid] = cnt;
     if (!sync(0, [&] {
           const int64_t tot = prefix_blocks();
           if (threadIdx.x == 0) {
@@ -401,7 +444,7 @@ struct K {
       return false;
     // stable compaction into the other buffer
     int2* dst = sel ? B.al0 : B.al1;
-    int64_t run = ldcg(B.blk_a + blockIdx.x);
+    int64_t run = ldcg(B.blk_a + bid);
     for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
       int2 a[kScanU];
       bool alive[kScanU];
@@ -458,7 +501,7 @@ struct K {
       }
     }
     mx = block_max<int64_t>(mx, S->scr);
-    if (threadIdx.x == 0) B.blk_b[blockIdx.x] = mx;
+    if (threadIdx.x == 0) B.blk_b[bid] = mx;
     return sync(0, [&] {
       const int64_t m = max_blocks_signed();
       co_after_heavy((int32_t)m);
@@ -500,7 +543,7 @@ struct K {
     }
     cnt = block_sum<int64_t>(cnt, S->scr);
     mx = block_max<int64_t>(mx, S->scr);
-    if (threadIdx.x == 0) { B.blk_a[blockIdx.x] = cnt; B.blk_b[blockIdx.x] = mx; }
+    if (threadIdx.x == 0) { B.blk_a[bid] = cnt; B.blk_b[bid] = mx; }
     if (!sync(0, [&] {
           const int64_t tot = prefix_blocks();
           const int64_t D = max_blocks_signed();
@@ -516,7 +559,7 @@ struct K {
       return false;
     const int32_t tau = P().th;
     int32_t* dst = (flags & 2) ? B.nz0 : ((flags & 1) ? B.nz0 : B.nz1);
-    int64_t run = ldcg(B.blk_a + blockIdx.x);
+    int64_t run = ldcg(B.blk_a + bid);
     for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
       int32_t v[kScanU];
       uint32_t d[kScanU];
@@ -652,7 +695,7 @@ struct K {
           cnt += (a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi) ? 1 : 0;
       }
       cnt = block_sum<int64_t>(cnt, S->scr);
-      if (threadIdx.x == 0) B.blk_a[blockIdx.x] = cnt;
+      if (threadIdx.x == 0) B.blk_a[bid] = cnt;
       if (!sync(2, [&] {
             const int64_t tot = prefix_blocks();
             if (threadIdx.x == 0) {
@@ -664,7 +707,7 @@ struct K {
       // S2: emit the first `take` alive entries of the window
       const int64_t take = P().take, need = P().need;
       const bool first_window = P().r0 < 0;
-      int64_t run = ldcg(B.blk_a + blockIdx.x);
+      int64_t run = ldcg(B.blk_a + bid);
       if (run < take) {
         for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
           int2 a[kScanU];
@@ -774,7 +817,7 @@ struct K {
 
   __device__ void attach_from_actives(bool skip_blocked) {
     const int64_t an = P().act_n, aE = P().act_E;
-    lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
+    lbs(B.act_e, an, aE, [&](const Lbs& L) {
       bool push[kLbsK];
       int32_t u[kLbsK];
       unsigned long long x[kLbsK];
@@ -795,7 +838,7 @@ struct K {
   __device__ void c4_detect() {
     const int64_t an = P().act_n, aE = P().act_E;
     const int32_t r0 = P().r0;
-    lbs_for_each(B.act_e, an, aE, lbs_ws(), [&](const Lbs& L) {
+    lbs(B.act_e, an, aE, [&](const Lbs& L) {
       int32_t u[kLbsK];
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) u[q] = L.ok(q) ? __ldg(B.col + L.csr(q)) : 0;
@@ -813,7 +856,7 @@ struct K {
   __device__ void c4_classify() {
     const int64_t an = P().act_n;
     const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t gw = ((int64_t)bid * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)G * blockDim.x) >> 5;
     for (int64_t base = gw * 32; base < an; base += nw * 32) {
       const int64_t j = base + lane;
@@ -838,7 +881,7 @@ struct K {
   // Reset the per-item scratch of the blocked list (after its counter is known).
   __device__ void c4_blocked_init() {
     const int64_t bn = P().b_n;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
+    for (int64_t q = bid * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
       B.hit_c[q] = 0;
       B.hit_p[q] = 0;
       B.pull[q] = 0x7FFFFFFF;
@@ -850,7 +893,7 @@ struct K {
   __device__ void c4_fix_scan() {
     const int64_t bn = P().b_n, bE = P().b_E;
     const int32_t r0 = P().r0;
-    lbs_for_each(B.b_e, bn, bE, lbs_ws(), [&](const Lbs& L) {
+    lbs(B.b_e, bn, bE, [&](const Lbs& L) {
 #pragma unroll
       for (int i = 0; i < kLbsK; ++i) {
         if (!L.ok(i)) continue;
@@ -873,7 +916,7 @@ struct K {
   __device__ long long c4_fix_decide() {
     const int64_t bn = P().b_n;
     long long left = 0;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
+    for (int64_t q = bid * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
       const int32_t j = ldcg(B.b_j + q);
       const int32_t v = ldcg(B.act_v + j), r = ldcg(B.act_r + j);
       if (lo_of(ldcg(B.st + v)) != kUndecided) continue;
@@ -891,7 +934,7 @@ struct K {
   __device__ void c4_blocked_attach() {
     const int64_t bn = P().b_n, bE = P().b_E;
     const int32_t r0 = P().r0;
-    lbs_for_each(B.b_e, bn, bE, lbs_ws(), [&](const Lbs& L) {
+    lbs(B.b_e, bn, bE, [&](const Lbs& L) {
 #pragma unroll
       for (int i = 0; i < kLbsK; ++i) {
         bool push = false;
@@ -920,7 +963,7 @@ struct K {
   __device__ void c4_pull_finalize() {
     const int64_t bn = P().b_n;
     const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t gw = ((int64_t)bid * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)G * blockDim.x) >> 5;
     for (int64_t base = gw * 32; base < bn; base += nw * 32) {
       const int64_t q = base + lane;
@@ -948,7 +991,7 @@ struct K {
   // ---------------- removal: residual degrees and the objective --------------
   __device__ void decrement() {
     const int64_t nn = P().new_n, nE = P().new_E;
-    lbs_for_each(B.new_e, nn, nE, lbs_ws(), [&](const Lbs& L) {
+    lbs(B.new_e, nn, nE, [&](const Lbs& L) {
       int32_t w[kLbsK], lu[kLbsK];
       unsigned long long x[kLbsK];
 #pragma unroll
@@ -986,18 +1029,16 @@ struct K {
   }
 };
 
-__global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ RoundBuffers B) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Shared& S = *reinterpret_cast<Shared*>(smem_raw);
-  K k{B, B.ctl, &S, gridDim.x, 0u, Tally{0, 0, 0, 0, 0, 0}};
-  if ((threadIdx.x & 31) == 0) S.app[threadIdx.x >> 5].n = 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+// All rounds of one clustering job, run by the team of blocks in k.  The
+// state words, the control block and the lists in k.B belong to this job.
+__device__ void run_job(K& k, int algo) {
+  Shared& S = *k.S;
+  Ctl* C = k.C;
+  if (k.bid == 0 && threadIdx.x == 0) {
     for (int i = 0; i < 8; ++i) S.co.ph_ns[i] = 0;
     S.co.t0 = globaltimer_ns();
   }
   __syncthreads();
-  Ctl* C = B.ctl;
-  const int algo = vload(&C->algo);
   if (!k.sync(7, [&] { k.co_init(); })) goto out;
 
   for (;;) {
@@ -1072,11 +1113,224 @@ __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ 
   }
 out:
   // coordinator: results for the host
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (k.bid == 0 && threadIdx.x == 0) {
     C->round = S.co.round;
     C->n_alive = S.co.n_alive;
     C->done = S.plan.state == kDone ? 1 : 0;
     for (int i = 0; i < 8; ++i) C->ph_ns[i] = S.co.ph_ns[i];
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ RoundBuffers B) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shared& S = *reinterpret_cast<Shared*>(smem_raw);
+  K k{B, B.ctl, &S, gridDim.x, blockIdx.x, 0u, Tally{0, 0, 0, 0, 0, 0}};
+  if ((threadIdx.x & 31) == 0) S.u.w.app[threadIdx.x >> 5].n = 0;
+  __syncthreads();
+  run_job(k, vload(&B.ctl->algo));
+}
+
+
+// ---------------------------------------------------------------------------
+// Batched engine: many (graph, permutation) jobs in one persistent launch.
+// The grid is cut into teams of G blocks; team t runs jobs t, t + T, ...
+// (jobs arrive sorted by size, largest first).  A job is the whole pipeline:
+// permutation, state set-up, all rounds, objective.  Each team owns one
+// scratch slot, reused job after job.
+// ---------------------------------------------------------------------------
+
+// pi for the job in k.B, computed by the team: bucket by the top key bits
+// (histogram, exclusive scan, scatter), then a counting sort on the next
+// kPermSubBits bits plus an insertion sort inside each bucket.  Also writes
+// the initial state words.
+__device__ bool team_permutation(K& k, uint64_t seed) {
+  const RoundBuffers& B = k.B;
+  Shared& S = *k.S;
+  const int64_t n = B.n;
+  int bits = 0;
+  while (bits < 12 && (n >> bits) > 768) ++bits;
+  const int nb = 1 << bits;
+  int64_t* cursor = B.pcnt;            // nb counts, then cursors
+  int64_t* start = B.pcnt + nb + 1;    // nb + 1 bucket starts
+  const int64_t tid = (int64_t)k.bid * blockDim.x + threadIdx.x, nthr = (int64_t)k.G * blockDim.x;
+  // 1: histogram (shared memory, then one global add per non-empty bucket) and state words
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) S.u.perm.hist[i] = 0;
+  __syncthreads();
+  for (int64_t v = tid; v < n; v += nthr) {
+    const uint64_t key = perm_key(seed, (uint64_t)v);
+    atomicAdd(&S.u.perm.hist[bits == 0 ? 0 : (int)(key >> (64 - bits))], 1);
+    const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
+    B.st[v] = word(kAliveHi, (uint32_t)d);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    const int h = S.u.perm.hist[i];
+    if (h) atomicAdd(reinterpret_cast<unsigned long long*>(cursor + i), (unsigned long long)h);
+  }
+  if (!k.sync(7, [&] {
+        int64_t run = 0;
+        for (int base = 0; base < nb; base += blockDim.x) {
+          const int b = base + threadIdx.x;
+          const int64_t c = b < nb ? ldcg(cursor + b) : 0;
+          int64_t tot;
+          const int64_t ex = block_exclusive_sum<int64_t>(c, S.scr, &tot);
+          if (b < nb) { start[b] = run + ex; cursor[b] = run + ex; }
+          run += tot;
+        }
+        if (threadIdx.x == 0) start[nb] = run;
+      }))
+    return false;
+  // 2: scatter
+  for (int64_t v = tid; v < n; v += nthr) {
+    const uint64_t key = perm_key(seed, (uint64_t)v);
+    const int b = bits == 0 ? 0 : (int)(key >> (64 - bits));
+    const int64_t pos = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cursor + b), 1ull);
+    B.ptmp[pos] = (int32_t)v;
+  }
+  if (!k.sync(7)) return false;
+  // 3: sort each bucket by (key, v)
+  PermSmem& P = S.u.perm;
+  const int shift = 64 - bits - kPermSubBits;
+  for (int b = (int)k.bid; b < nb; b += (int)k.G) {
+    const int64_t s0 = ldcg(start + b), len = ldcg(start + b + 1) - s0;
+    if (len <= 0) continue;
+    if (len > kPermCap) {
+      // rare: rank by counting (exact, quadratic)
+      for (int64_t i = threadIdx.x; i < len; i += blockDim.x) {
+        const int32_t vi = ldcg(B.ptmp + s0 + i);
+        const uint64_t ki = perm_key(seed, (uint64_t)vi);
+        int64_t r = 0;
+        for (int64_t j = 0; j < len; ++j) {
+          const int32_t vj = ldcg(B.ptmp + s0 + j);
+          const uint64_t kj = perm_key(seed, (uint64_t)vj);
+          r += (kj < ki || (kj == ki && vj < vi)) ? 1 : 0;
+        }
+        B.order_w[s0 + r] = vi;
+      }
+      __syncthreads();
+      continue;
+    }
+    for (int i = threadIdx.x; i < kPermSub; i += blockDim.x) P.cnt[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const int32_t v = ldcg(B.ptmp + s0 + i);
+      const uint64_t key = perm_key(seed, (uint64_t)v);
+      P.sv[i] = v;
+      P.sk[i] = key;
+      atomicAdd(&P.cnt[(int)((key >> shift) & (kPermSub - 1))], 1);
+    }
+    __syncthreads();
+    {
+      const int i0 = threadIdx.x * 2;
+      const int c0 = i0 < kPermSub ? P.cnt[i0] : 0, c1 = i0 + 1 < kPermSub ? P.cnt[i0 + 1] : 0;
+      int64_t tot;
+      const int64_t ex = block_exclusive_sum<int64_t>(c0 + c1, S.scr, &tot);
+      if (i0 < kPermSub) P.cnt[i0] = (int)ex;
+      if (i0 + 1 < kPermSub) P.cnt[i0 + 1] = (int)ex + c0;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+      const uint64_t key = P.sk[i];
+      const int pos = atomicAdd(&P.cnt[(int)((key >> shift) & (kPermSub - 1))], 1);
+      P.ok[pos] = key;
+      P.ov[pos] = P.sv[i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kPermSub; q += blockDim.x) {
+      const int lo = q == 0 ? 0 : P.cnt[q - 1], hi = P.cnt[q];
+      for (int i = lo + 1; i < hi; ++i) {
+        const uint64_t key = P.ok[i];
+        const int32_t v = P.ov[i];
+        int j = i - 1;
+        while (j >= lo && (key < P.ok[j] || (key == P.ok[j] && v < P.ov[j]))) {
+          P.ok[j + 1] = P.ok[j];
+          P.ov[j + 1] = P.ov[j];
+          --j;
+        }
+        P.ok[j + 1] = key;
+        P.ov[j + 1] = v;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < len; i += blockDim.x) B.order_w[s0 + i] = P.ov[i];
+    __syncthreads();
+  }
+  return k.sync(7);
+}
+
+__global__ void __launch_bounds__(kThreads, 2)
+k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__ slots, int team_size, int algo,
+        int64_t eps_ppm) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Shared& S = *reinterpret_cast<Shared*>(smem_raw);
+  __shared__ RoundBuffers rb;
+  const unsigned G = (unsigned)team_size;
+  const unsigned team = blockIdx.x / G, nteams = gridDim.x / G;
+  if (team >= nteams) return;
+  Ctl* C = slots[team].ctl;
+  K k{rb, C, &S, G, blockIdx.x % G, 0u, Tally{0, 0, 0, 0, 0, 0}};
+  if (threadIdx.x == 0) S.plan.state = kDone;
+  __syncthreads();
+  for (int j = (int)team; j < njobs; j += (int)nteams) {
+    if (threadIdx.x == 0) {
+      rb = slots[team];
+      const BatchJob& jb = jobs[j];
+      rb.n = jb.n;
+      rb.nnz = jb.nnz;
+      rb.max_deg = jb.max_deg;
+      rb.off = jb.off;
+      rb.col = jb.col;
+      rb.nz_static = jb.nz;
+      rb.nz_n = jb.nz_n;
+      rb.order = rb.order_w;
+      rb.stats = nullptr;
+      rb.stats_cap = 0;
+    }
+    __syncthreads();
+    // zero the permutation counters, reset the control block (not the barrier counters)
+    const int64_t zn = 2 * (int64_t)kPermMaxBuckets + 2;
+    for (int64_t i = (int64_t)k.bid * blockDim.x + threadIdx.x; i < zn; i += (int64_t)G * blockDim.x) rb.pcnt[i] = 0;
+    if (!k.sync(7, [&] {
+          if (threadIdx.x == 0) {
+            C->err = 0;
+            C->algo = algo;
+            C->eps_ppm = eps_ppm;
+            C->mc = 0; C->mm = 0; C->pairs = 0;
+            C->undecided = 0; C->h_pack = 0;
+            S.plan.state = kRun;
+          }
+        }))
+      break;
+    if (!team_permutation(k, jobs[j].seed)) break;
+    if ((threadIdx.x & 31) == 0) S.u.w.app[threadIdx.x >> 5].n = 0;
+    __syncthreads();
+    run_job(k, algo);
+    if (S.plan.state == kAbort) {
+      if (k.bid == 0 && threadIdx.x == 0) jobs[j].err = ld_volatile_int(&C->err) ? ld_volatile_int(&C->err) : kErrInternal;
+      break;
+    }
+    // pair term of the objective (see k_finalize_labels)
+    unsigned long long pairs = 0;
+    for (int64_t v = (int64_t)k.bid * blockDim.x + threadIdx.x; v < rb.n; v += (int64_t)G * blockDim.x) {
+      const int32_t c = decode_label(hi_of(ldcg(rb.st + v)));
+      if (c >= 0 && c < rb.n && ldcg(rb.order + c) == v) {
+        const unsigned long long sz = 1ull + (unsigned long long)ldcg(rb.size + c);
+        pairs += sz * (sz - 1) / 2;
+      }
+    }
+    pairs = (unsigned long long)block_sum<int64_t>((int64_t)pairs, S.scr);
+    if (threadIdx.x == 0 && pairs) atomicAdd(&C->pairs, pairs);
+    if (!k.sync(6, [&] {
+          if (threadIdx.x == 0) {
+            BatchJob& jb = jobs[j];
+            const int done = S.plan.state == kDone && S.co.n_alive == 0;
+            jb.rounds = S.co.round;
+            jb.D = jb.nnz / 2 - 2 * (int64_t)vload(&C->mc) - (int64_t)vload(&C->mm) + (int64_t)vload(&C->pairs);
+            jb.err = done ? 0 : kErrInternal;
+            S.plan.state = kDone;
+          }
+        }))
+      break;
   }
 }
 
@@ -1201,6 +1455,42 @@ cudaError_t launch_finalize_labels(const RoundBuffers& b, int32_t* labels_out, c
   const int grid = (int)(want < 2048 ? want : 2048);
   k_finalize_labels<<<grid, 256, 0, stream>>>(b, labels_out);
   return cudaGetLastError();
+}
+
+
+int batch_grid_size(int device) {
+  int sms = 0, per = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared));
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch, kThreads, sizeof(Shared));
+  if (per < 1) per = 1;
+  if (per > 2) per = 2;
+  return sms * per;
+}
+
+size_t batch_slot_bytes(int64_t n_max, int team_size) {
+  const size_t nn = (size_t)(n_max > 0 ? n_max : 1);
+  return rounds_workspace_bytes(n_max, 0, team_size) + 2 * align_up(4 * nn) +
+         align_up(8 * (2 * (size_t)kPermMaxBuckets + 2));
+}
+
+void batch_slot_carve(void* ws, int64_t n_max, int team_size, RoundBuffers* B) {
+  const size_t nn = (size_t)(n_max > 0 ? n_max : 1);
+  rounds_carve(ws, n_max, 0, team_size, B);
+  char* p = static_cast<char*>(ws) + rounds_workspace_bytes(n_max, 0, team_size);
+  B->order_w = reinterpret_cast<int32_t*>(p); p += align_up(4 * nn);
+  B->ptmp = reinterpret_cast<int32_t*>(p); p += align_up(4 * nn);
+  B->pcnt = reinterpret_cast<int64_t*>(p);
+  B->order = B->order_w;
+}
+
+cudaError_t launch_batch(const BatchJob* jobs_dev, int njobs, const RoundBuffers* slots_dev, int team_size,
+                         int grid, int algo, int64_t eps_ppm, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared));
+  if (e != cudaSuccess) return e;
+  BatchJob* jobs = const_cast<BatchJob*>(jobs_dev);
+  void* args[] = {&jobs, &njobs, &slots_dev, &team_size, &algo, &eps_ppm};
+  return cudaLaunchCooperativeKernel((const void*)k_batch, dim3(grid), dim3(kThreads), args, sizeof(Shared), stream);
 }
 
 }  // namespace ccg

@@ -86,6 +86,8 @@ def load(build_if_missing: bool = True):
         lib.cc_last_phase_times.argtypes = [vp, vp, i32]
         lib.cc_disagreements_static.restype = ci
         lib.cc_disagreements_static.argtypes = [i64, vp, vp, vp, vp, vp]
+        lib.cc_batch_jobs.restype = ci
+        lib.cc_batch_jobs.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp]
         lib.cc_batch_run.restype = ci
         lib.cc_batch_run.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp, vp, vp]
         _lib = lib
@@ -223,6 +225,20 @@ class Graph:
         d = ctypes.c_int64()
         _check("cc_disagreements", self._lib.cc_disagreements(self._h, _ptr(labels), ctypes.byref(d)))
         return d.value
+
+
+def batch_jobs(graphs, algo="cw", eps=0.5, seeds=None, k_perms=8):
+    """Every (graph, permutation) job of a batch: (D, rounds), each shaped
+    (len(graphs), k_perms); job (i, j) uses seed seeds[i] + j."""
+    lib = load()
+    cnt = len(graphs)
+    seeds = np.asarray(seeds if seeds is not None else np.zeros(cnt), dtype=np.uint64)
+    hs = (ctypes.c_void_p * max(cnt, 1))(*[g._h.value for g in graphs])
+    d = np.zeros(max(cnt * k_perms, 1), np.int64)
+    r = np.zeros(max(cnt * k_perms, 1), np.int32)
+    _check("cc_batch_jobs", lib.cc_batch_jobs(hs, cnt, ALGOS[algo], float(eps), seeds.ctypes.data, k_perms,
+                                              d.ctypes.data, r.ctypes.data))
+    return d[:cnt * k_perms].reshape(cnt, k_perms), r[:cnt * k_perms].reshape(cnt, k_perms)
 
 
 def batch_run(graphs, algo="cw", eps=0.5, seeds=None, k_perms=8, want_labels=False):

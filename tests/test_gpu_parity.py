@@ -191,3 +191,58 @@ def test_planted_partition_1m_all_eps(cc, ora, gg):
             lab, r, d = graph.cluster("cw", eps, 0)
             assert np.array_equal(lab, olab) and r == orr
             assert d == ora.disagreements(g.off, g.col, olab)
+
+
+# --------------------------------------------------------------------------
+# Batched engine (many graphs x k permutations in one launch per size class)
+# --------------------------------------------------------------------------
+def batch_graphs(gg):
+    """Chung-Lu power-law graphs across the batch size classes: one block per
+    job (n <= 2^16) and eight-block teams (2^16 < n <= 2^21)."""
+    sizes = [(300, 8.0), (1000, 12.0), (2500, 30.0), (9000, 16.0), (30000, 20.0), (65536, 8.0),
+             (80000, 10.0), (250000, 24.0)]
+    return [gg.chung_lu(n, d, seed=40 + i) for i, (n, d) in enumerate(sizes)]
+
+
+@pytest.mark.parametrize("algo", ["cw", "c4"])
+def test_batch_jobs_match_oracle(cc, ora, gg, algo):
+    a = 1 if algo == "c4" else 2
+    gs = batch_graphs(gg)
+    graphs = [cc.Graph(g.off, g.col) for g in gs]
+    try:
+        seeds = np.array([17 * i + 3 for i in range(len(gs))], np.uint64)
+        k = 3
+        D, R = cc.batch_jobs(graphs, algo, 0.5, seeds, k)
+        for i, g in enumerate(gs):
+            for j in range(k):
+                order = ora.permutation(g.n, int(seeds[i]) + j)
+                lab, r, _, _ = ora.rounds(g.off, g.col, order, a, 0.5)
+                assert R[i, j] == r, (i, j)
+                assert D[i, j] == ora.disagreements(g.off, g.col, lab), (i, j)
+        # each job gives the same result alone and inside the batch
+        for i in (0, len(gs) - 1):
+            _, r, d = graphs[i].cluster(algo, 0.5, int(seeds[i]) + 1, want_labels=False)
+            assert (r, d) == (R[i, 1], D[i, 1])
+    finally:
+        for x in graphs:
+            x.close()
+
+
+def test_batch_run_best_of_k(cc, ora, gg):
+    gs = batch_graphs(gg)[:5]
+    graphs = [cc.Graph(g.off, g.col) for g in gs]
+    try:
+        seeds = np.arange(len(gs), dtype=np.uint64) * 1000
+        bj, bd, br, labels = cc.batch_run(graphs, "cw", 0.9, seeds, 4, want_labels=True)
+        for i, g in enumerate(gs):
+            costs = []
+            for j in range(4):
+                order = ora.permutation(g.n, int(seeds[i]) + j)
+                lab, r, _, _ = ora.rounds(g.off, g.col, order, 2, 0.9)
+                costs.append((ora.disagreements(g.off, g.col, lab), j, lab, r))
+            best = min(costs, key=lambda c: (c[0], c[1]))
+            assert (bj[i], bd[i], br[i]) == (best[1], best[0], best[3])
+            assert np.array_equal(labels[i], best[2])
+    finally:
+        for x in graphs:
+            x.close()
