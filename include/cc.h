@@ -216,6 +216,35 @@ int cc_last_phase_times(const cc_graph* g, double* ms_out, int32_t cap);
 int cc_disagreements_static(int64_t n, const int64_t* row_offsets, const int32_t* col_idx,
                             const int32_t* labels, int64_t* out, void* cuda_stream);
 
+/*
+ * Serving loop with continuous batching.  cc_server_submit queues a request
+ * (graph g, algo, eps, seed) and returns a ticket at once.  A dispatcher
+ * thread starts the waiting requests as one batched launch (one thread block
+ * per request) on one of three streams as soon as a stream is free and the
+ * device-memory budget covers the batch's scratch, so requests that arrive
+ * while others run are admitted and overlap with them.  Graphs stay resident
+ * (they are the caller's, and must outlive their requests); graphs above 2^16
+ * vertices run on the whole GPU one at a time.  The result of a request is
+ * exactly that of cc_cluster with the same arguments.
+ *   mem_budget   bytes of device memory for batch scratch (a request whose
+ *                scratch alone exceeds it fails with CC_ERR_OOM).
+ *   max_batch    largest number of requests per launch.
+ *   labels_out   device int32[n] or NULL.
+ * cc_server_poll returns CC_ERR_BUSY while the request is pending;
+ * cc_server_wait blocks (at most 10 minutes).  latency_ms = time from submit
+ * to completion as seen by the dispatcher.  cc_server_destroy finishes the
+ * queued work first.  A server is thread safe.
+ */
+typedef struct cc_server cc_server;
+int cc_server_create(size_t mem_budget, int32_t max_batch, cc_server** out);
+int cc_server_submit(cc_server* s, cc_graph* g, int algo, double eps, uint64_t seed,
+                     int32_t* labels_out, int64_t* ticket);
+int cc_server_poll(cc_server* s, int64_t ticket, int32_t* rounds, int64_t* disagreements,
+                   double* latency_ms);
+int cc_server_wait(cc_server* s, int64_t ticket, int32_t* rounds, int64_t* disagreements,
+                   double* latency_ms);
+int cc_server_destroy(cc_server* s);
+
 /* Human-readable name of a status code (static storage). */
 const char* cc_status_string(int status);
 

@@ -5,8 +5,8 @@ The bulk-synchronous rounds of "Parallel Correlation Clustering on Big Graphs"
 sm_103a CUDA kernels behind the C ABI of ``include/cc.h``.  This package is a
 thin ctypes binding over that library.
 """
-from .native import (ALGOS, C4, CLUSTERWILD, CCError, Graph, ROUND_STAT_FIELDS, batch_jobs, batch_run,
-                     lib_path, load)
+from .native import (ALGOS, C4, CLUSTERWILD, CCError, Graph, ROUND_STAT_FIELDS, Server, batch_jobs,
+                     batch_run, lib_path, load)
 
-__all__ = ["ALGOS", "C4", "CLUSTERWILD", "CCError", "Graph", "ROUND_STAT_FIELDS", "batch_jobs", "batch_run",
-           "lib_path", "load"]
+__all__ = ["ALGOS", "C4", "CLUSTERWILD", "CCError", "Graph", "ROUND_STAT_FIELDS", "Server", "batch_jobs",
+           "batch_run", "lib_path", "load"]

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/cc.h"
+#include "cc_graph_impl.h"
 #include "cc_internal.h"
 
 using namespace ccg;
@@ -21,43 +22,6 @@ constexpr int64_t kBatchSmallN = 1 << 16;
 constexpr int64_t kBatchTeamN = 1 << 21;
 constexpr int kBatchTeamBlocks = 8;
 }  // namespace
-
-struct cc_graph {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  int num_sms = 0;
-  int64_t n = 0, nnz = 0;
-  int32_t max_deg = 0;
-  int64_t* off = nullptr;
-  int32_t* col = nullptr;
-  bool own_off = false, own_col = false;
-  int32_t* nz_row = nullptr;
-  int64_t* nz_pos = nullptr;
-  int64_t nz_n = 0;
-  // cached workspaces (grown on demand)
-  void* perm_ws = nullptr;
-  size_t perm_ws_bytes = 0;
-  int32_t* order = nullptr;
-  void* round_ws = nullptr;
-  size_t round_ws_bytes = 0;
-  int grid = 0;
-  int32_t* labels_tmp = nullptr;
-  void* obj_ws = nullptr;
-  unsigned long long* obj_out = nullptr;
-  RoundStat* stats_dev = nullptr;
-  int64_t stats_dev_cap = 0;
-  int* perm_err = nullptr;
-  // optional event timing of the last clustering
-  bool timing = false;
-  bool timed = false;
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  float last_ms[3] = {0, 0, 0};
-  unsigned long long last_phase_ns[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  bool phases_valid = false;
-  // pinned host staging for the small results
-  Ctl* ctl_host = nullptr;
-  unsigned long long* obj_host = nullptr;
-};
 
 namespace {
 

@@ -114,6 +114,7 @@ struct BatchJob {
   int32_t max_deg;
   int32_t err;          // result: device status (0 = ok, 1 = not run)
   uint64_t seed;
+  int32_t* labels;      // optional device int32[n]: center vertex id of each vertex
   int64_t rounds;       // result
   int64_t D;            // result: disagreements
 };
@@ -125,6 +126,9 @@ size_t batch_slot_bytes(int64_t n_max, int team_size);
 void batch_slot_carve(void* ws, int64_t n_max, int team_size, RoundBuffers* B);
 cudaError_t launch_batch(const BatchJob* jobs_dev, int njobs, const RoundBuffers* slots_dev, int team_size,
                          int grid, int algo, int64_t eps_ppm, cudaStream_t stream);
+// Team size 1 with an ordinary (not cooperative) launch of `blocks` blocks.
+cudaError_t launch_batch_blocks(const BatchJob* jobs_dev, int njobs, const RoundBuffers* slots_dev, int blocks,
+                                int algo, int64_t eps_ppm, cudaStream_t stream);
 
 size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid);
 // Carve a workspace of rounds_workspace_bytes() into RoundBuffers (pointers only).

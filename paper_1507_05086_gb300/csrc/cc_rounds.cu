@@ -1309,11 +1309,15 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
       if (k.bid == 0 && threadIdx.x == 0) jobs[j].err = ld_volatile_int(&C->err) ? ld_volatile_int(&C->err) : kErrInternal;
       break;
     }
-    // pair term of the objective (see k_finalize_labels)
+    // labels and the pair term of the objective (see k_finalize_labels)
     unsigned long long pairs = 0;
+    int32_t* const lab = jobs[j].labels;
     for (int64_t v = (int64_t)k.bid * blockDim.x + threadIdx.x; v < rb.n; v += (int64_t)G * blockDim.x) {
       const int32_t c = decode_label(hi_of(ldcg(rb.st + v)));
-      if (c >= 0 && c < rb.n && ldcg(rb.order + c) == v) {
+      if (c < 0 || c >= rb.n) { k.fail(kErrInternal); continue; }
+      const int32_t cv = ldcg(rb.order + c);
+      if (lab) lab[v] = cv;
+      if (cv == v) {
         const unsigned long long sz = 1ull + (unsigned long long)ldcg(rb.size + c);
         pairs += sz * (sz - 1) / 2;
       }
@@ -1482,6 +1486,17 @@ void batch_slot_carve(void* ws, int64_t n_max, int team_size, RoundBuffers* B) {
   B->ptmp = reinterpret_cast<int32_t*>(p); p += align_up(4 * nn);
   B->pcnt = reinterpret_cast<int64_t*>(p);
   B->order = B->order_w;
+}
+
+// One block per job (team size 1): no block waits on another, so an
+// ordinary launch suffices and several batches can share the GPU.
+cudaError_t launch_batch_blocks(const BatchJob* jobs_dev, int njobs, const RoundBuffers* slots_dev, int blocks,
+                                int algo, int64_t eps_ppm, cudaStream_t stream) {
+  cudaError_t e = cudaFuncSetAttribute(k_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Shared));
+  if (e != cudaSuccess) return e;
+  k_batch<<<blocks, kThreads, sizeof(Shared), stream>>>(const_cast<BatchJob*>(jobs_dev), njobs, slots_dev, 1, algo,
+                                                       eps_ppm);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_batch(const BatchJob* jobs_dev, int njobs, const RoundBuffers* slots_dev, int team_size,

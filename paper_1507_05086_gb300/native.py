@@ -88,6 +88,16 @@ def load(build_if_missing: bool = True):
         lib.cc_disagreements_static.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.cc_batch_jobs.restype = ci
         lib.cc_batch_jobs.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp]
+        lib.cc_server_create.restype = ci
+        lib.cc_server_create.argtypes = [ctypes.c_size_t, i32, ctypes.POINTER(vp)]
+        lib.cc_server_submit.restype = ci
+        lib.cc_server_submit.argtypes = [vp, vp, ci, ctypes.c_double, u64, vp, vp]
+        lib.cc_server_poll.restype = ci
+        lib.cc_server_poll.argtypes = [vp, i64, vp, vp, vp]
+        lib.cc_server_wait.restype = ci
+        lib.cc_server_wait.argtypes = [vp, i64, vp, vp, vp]
+        lib.cc_server_destroy.restype = ci
+        lib.cc_server_destroy.argtypes = [vp]
         lib.cc_batch_run.restype = ci
         lib.cc_batch_run.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp, vp, vp]
         _lib = lib
@@ -260,3 +270,58 @@ def batch_run(graphs, algo="cw", eps=0.5, seeds=None, k_perms=8, want_labels=Fal
     _check("cc_batch_run", lib.cc_batch_run(hs, cnt, ALGOS[algo], float(eps), seeds.ctypes.data, k_perms,
                                             lab_arr, best_j.ctypes.data, best_d.ctypes.data, rounds.ctypes.data))
     return best_j, best_d, rounds, labels
+
+
+class Server:
+    """Serving loop with continuous batching (``cc_server_*``).
+
+    ``submit`` returns a ticket at once; requests waiting when a stream frees
+    up run together as one batched launch, overlapping with earlier batches,
+    within a device-memory budget for their scratch.
+    """
+
+    def __init__(self, mem_budget: int = 4 << 30, max_batch: int = 1024):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check("cc_server_create", self._lib.cc_server_create(int(mem_budget), int(max_batch), ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, graph: Graph, algo="cw", eps: float = 0.5, seed: int = 0, labels_out=None) -> int:
+        t = ctypes.c_int64()
+        _check("cc_server_submit", self._lib.cc_server_submit(self._h, graph._h, ALGOS[algo], float(eps),
+                                                              seed & (2**64 - 1), _ptr(labels_out),
+                                                              ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int):
+        """None while pending, else (rounds, disagreements, latency_ms)."""
+        r, d, ms = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
+        rc = self._lib.cc_server_poll(self._h, ticket, ctypes.byref(r), ctypes.byref(d), ctypes.byref(ms))
+        if rc == -6:
+            return None
+        _check("cc_server_poll", rc)
+        return r.value, d.value, ms.value
+
+    def wait(self, ticket: int):
+        """(rounds, disagreements, latency_ms) of a request, blocking."""
+        r, d, ms = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_double()
+        _check("cc_server_wait", self._lib.cc_server_wait(self._h, ticket, ctypes.byref(r), ctypes.byref(d),
+                                                          ctypes.byref(ms)))
+        return r.value, d.value, ms.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.cc_server_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
