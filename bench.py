@@ -43,6 +43,10 @@ def parse_args(argv=None):
     p.add_argument("--algos", default="cw,c4")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch-graphs", type=int, default=256,
+                   help="Chung-Lu graphs in the batched-jobs measurement (0 = skip)")
+    p.add_argument("--serve-seconds", type=float, default=2.0,
+                   help="length of the Poisson arrival stream for the serving measurement (0 = skip)")
     return p.parse_args(argv)
 
 
@@ -149,6 +153,95 @@ def cpu_sample_run(algos, eps, seed_base=7):
         oracle.rounds(g.off, g.col, order, 1 if a == "c4" else 2, eps, 1)
     dt = time.perf_counter() - t0
     return g.m * len(algos), dt
+
+
+def batch_workload(count: int, base_seed: int = 0):
+    """Chung-Lu graphs (exponent 2.1) with n log-uniform in [1e3, 3e4] and mean
+    degree uniform in [8, 64], seed base + g: a bounded slice of the
+    4,096-graph batch (whose n reaches 1e6)."""
+    import concurrent.futures
+
+    import graphgen
+    import numpy as np
+    graphgen.build()
+    params = []
+    for g in range(count):
+        r = np.random.default_rng(base_seed + g)
+        params.append((int(round(10 ** (3 + np.log10(30.0) * r.random()))), 8.0 + 56.0 * r.random(), base_seed + g))
+    with concurrent.futures.ThreadPoolExecutor(16) as ex:
+        return list(ex.map(lambda p: graphgen.chung_lu(p[0], p[1], seed=p[2], threads=1), params))
+
+
+def measure_batch(cc, torch, gs, k_perms: int, eps: float, algo: str = "cw"):
+    """Jobs/s of the batched launch against one launch per job."""
+    import numpy as np
+    graphs = [cc.Graph(g.off, g.col) for g in gs]
+    try:
+        seeds = np.arange(len(gs), dtype=np.uint64) * 1000
+        cc.batch_jobs(graphs[:8], algo, eps, seeds[:8], 2)          # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        D, R = cc.batch_jobs(graphs, algo, eps, seeds, k_perms)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        jobs = len(gs) * k_perms
+        # one launch per job on a sample of the jobs (same jobs, same results)
+        sample = list(range(0, len(gs), max(1, len(gs) // 64)))
+        t0 = time.perf_counter()
+        for i in sample:
+            for j in range(k_perms):
+                _, r, d = graphs[i].cluster(algo, eps, int(seeds[i]) + j, want_labels=False)
+                assert (r, d) == (R[i, j], D[i, j])
+        t_single = (time.perf_counter() - t0) / (len(sample) * k_perms)
+        return {"graphs": len(gs), "k_perms": k_perms, "jobs": jobs, "algo": algo, "eps": eps,
+                "jobs_per_s": jobs / t_batch, "ms": t_batch * 1e3,
+                "one_launch_per_job_jobs_per_s": 1.0 / t_single,
+                "speedup_vs_one_launch_per_job": (jobs / t_batch) * t_single,
+                "sum_n": int(sum(g.n for g in gs)), "sum_m": int(sum(g.m for g in gs)),
+                "workload": "Chung-Lu exponent 2.1, n log-uniform [1e3, 3e4], mean degree U[8, 64], best-of-k jobs"}
+    finally:
+        for x in graphs:
+            x.close()
+
+
+def measure_serving(cc, torch, gs, seconds: float, rate: float = 2000.0, eps: float = 0.5, algo: str = "cw"):
+    """Poisson arrivals at `rate` jobs/s through the serving loop: latency
+    percentiles and achieved throughput, against serving each request with
+    its own launch as it arrives."""
+    import numpy as np
+    graphs = [cc.Graph(g.off, g.col) for g in gs]
+    rng = np.random.default_rng(2000)
+    nreq = max(1, int(rate * seconds))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
+    which = rng.integers(0, len(gs), nreq)
+    try:
+        with cc.Server(mem_budget=8 << 30, max_batch=512) as srv:
+            srv.wait(srv.submit(graphs[0], algo, eps, 1))            # warm-up
+            t0 = time.perf_counter()
+            tickets = []
+            for q in range(nreq):
+                while time.perf_counter() - t0 < arrivals[q]:
+                    pass
+                tickets.append(srv.submit(graphs[int(which[q])], algo, eps, 77 + q))
+            lat = np.array([srv.wait(t)[2] for t in tickets])
+            t_total = time.perf_counter() - t0
+        # one launch per request, served in arrival order
+        t0 = time.perf_counter()
+        lat1 = []
+        for q in range(min(nreq, 400)):
+            while time.perf_counter() - t0 < arrivals[q]:
+                pass
+            graphs[int(which[q])].cluster(algo, eps, 77 + q, want_labels=False)
+            lat1.append((time.perf_counter() - t0 - arrivals[q]) * 1e3)
+        lat1 = np.array(lat1)
+        return {"rate_jobs_per_s": rate, "requests": nreq, "throughput_jobs_per_s": nreq / t_total,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "one_launch_per_job": {"requests": int(lat1.size), "p50_ms": float(np.percentile(lat1, 50)),
+                                       "p99_ms": float(np.percentile(lat1, 99))},
+                "algo": algo, "eps": eps}
+    finally:
+        for x in graphs:
+            x.close()
 
 
 def run_reference(args):
@@ -274,6 +367,14 @@ def run_ours(args):
                "what": "per step: cc_graph_create from pinned host CSR (copy + validation), one C4 and one "
                        "ClusterWild! cc_cluster with labels to pinned host memory, cc_graph_destroy"}
 
+    batch = serve = None
+    if rank == 0 and (args.batch_graphs > 0 or args.serve_seconds > 0):
+        bgs = batch_workload(max(args.batch_graphs, 64))
+        if args.batch_graphs > 0:
+            batch = measure_batch(cc, torch, bgs[:args.batch_graphs], 8, args.eps)
+        if args.serve_seconds > 0:
+            serve = measure_serving(cc, torch, bgs[:64], args.serve_seconds)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         e, dt = cpu_sample_run(algos, args.eps)
@@ -305,6 +406,8 @@ def run_ours(args):
             "gpu_launches": KERNELS_PER_CLUSTERING * clusterings,
             "roofline": roofline,
             "cpu_baseline": cpu,
+            "batch": batch,
+            "serve": serve,
         }
         print(json.dumps(line), flush=True)
     graph.close()
