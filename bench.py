@@ -66,6 +66,20 @@ def aggregate(edges_per_rank, ms_per_rank):
     return sum(edges_per_rank) / (t / 1e3), t
 
 
+def reduce_across_ranks(elapsed_ms: float, edges: int, world: int, device):
+    """Whole-job throughput over all ranks: total edges over the slowest
+    rank's time.  Every rank gets the same (value, max_ms)."""
+    if world <= 1:
+        return aggregate([edges], [elapsed_ms])
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device=device)
+    e = torch.tensor([float(edges)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return e.item() / (t.item() / 1e3), t.item()
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -324,15 +338,7 @@ def run_ours(args):
     elapsed = start.elapsed_time(end)
     clusterings = args.steps * len(algos)
     edges_done = m * clusterings
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed, float(edges_done)], dtype=torch.float64, device="cuda")
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        value, tmax = t[1].item() / (mx[0].item() / 1e3), mx[0].item()
-    else:
-        value, tmax = aggregate([edges_done], [elapsed])
+    value, tmax = reduce_across_ranks(elapsed, edges_done, world, torch.device("cuda", local_rank))
 
     # roofline of the dominant kernel (the persistent round kernel)
     peak, peak_kind = measured_hbm_peak()
