@@ -148,10 +148,10 @@ def measured_hbm_peak():
 
 def rounds_algorithmic_bytes(edges_scanned: int, n: int) -> int:
     """Bytes the round kernel must move for one clustering: every scanned
-    adjacency entry reads its 4-byte column id and the neighbour's 8-byte state
+    adjacency entry reads its 4-byte column id and the neighbour's 4-byte state
     word; every vertex costs its two row offsets (16), its own state read and
-    write (16) and its alive-list entry (4)."""
-    return 12 * edges_scanned + 36 * n
+    write (8) and its alive-list entry (8)."""
+    return 8 * edges_scanned + 32 * n
 
 
 def cpu_sample_run(algos, eps, seed_base=7):

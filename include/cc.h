@@ -69,7 +69,7 @@ extern "C" {
                                 reference (caller keeps them alive until destroy) */
 #define CC_OFFSETS_I32  4u   /* row_offsets is int32[n+1] instead of int64[n+1]  */
 
-/* Limits: 0 <= n <= 2^31 - 2 (INT32_MAX marks "unclustered"), nnz < 2^33. */
+/* Limits: 0 <= n <= 2^31 - 32 (a 32-bit state word per vertex), nnz < 2^33. */
 
 typedef struct cc_graph cc_graph;
 

@@ -67,7 +67,8 @@ struct RoundBuffers {
   const int64_t* off;
   const int32_t* col;
   const int32_t* order;
-  unsigned long long* st;      // per-vertex state word
+  uint32_t* st;                // per-vertex state word
+  int32_t* arank;              // rank of a vertex while it is active
   int2* al0;                   // alive lists: (rank, vertex), rank-ordered
   int2* al1;
   // row lists (see RowList in cc_device.cuh): vertex, first virtual edge,

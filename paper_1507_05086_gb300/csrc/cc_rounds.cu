@@ -9,30 +9,30 @@
 // one vector load.  Every wait is bounded.  The host is not involved between
 // rounds.
 //
-// Per-vertex state: one 64-bit word st[v] = (hi:int32, lo:uint32)
-//   alive ............ hi = 0x7FFFFFFF, lo = residual degree
-//   clustered ........ hi = center rank (>= 0), lo = 0
-//   active this round  hi = ~rank (< 0), lo = status (undecided/center/non-center)
-// Centers keep hi = ~rank after their round; decoding a label is
-// hi < 0 ? ~hi : hi.  Because rank order is the clustering order, every
-// round's actives have ranks above every earlier center, so "active this
-// round" is hi < 0 with ~hi >= r0 (the round's first active rank).
+// Per-vertex state: one 32-bit word st[v]
+//   alive ............ kAlive | residual degree
+//   clustered ........ kLab + center rank
+//   active this round  kActive / kActCenter / kActNon (undecided or
+//                      ClusterWild! center / C4 center / C4 non-center)
+// An active's rank is kept in arank[v]; a center keeps the active marker until
+// the next round starts, then takes kLab + its own rank.
 //
 // Attachment (createCluster, concurrency rule 2): a center of rank r lowers
-// st[u] with a 64-bit atomicMin of (r << 32).  Alive words compare above any
-// (r << 32), clustered and active words compare below their own center's, so
-// one compare-then-atomicMin does rule 2 and skips dead and active vertices.
+// st[u] with atomicMin(kLab + r).  Alive words compare above every label and
+// active markers below, so one compare-then-atomicMin does rule 2 and skips
+// clustered and active vertices.
 //
-// Residual degrees live in the low word, so the decrement that follows the
-// removal of a vertex is a fire-and-forget 32-bit atomic on the same cache
-// sector the alive test just read.  Delta_i (max residual degree, exact every
-// round) comes from a heavy list H: every alive vertex whose degree was >= tau
-// when H was built.  Degrees only fall, so if the largest current degree in H
-// is still >= tau it is the maximum over the whole graph; otherwise a rebuild
-// scans the compact list of alive non-isolated vertices, takes the exact
-// maximum D, sets tau = D/2 and refills H.  No work per decrement.
-// The rank-ordered alive list used for selection is compacted separately when
-// most of its live range is dead.
+// Residual degrees live in the alive word itself, so the decrement that
+// follows the removal of a vertex is a fire-and-forget atomic on the word the
+// alive test just read; half the footprint of a label/degree pair keeps more
+// of the randomly accessed state in L2.  Delta_i (max residual degree, exact
+// every round) comes from a heavy list H: every alive vertex whose degree was
+// >= tau when H was built.  Degrees only fall, so if the largest current
+// degree in H is still >= tau it is the maximum over the whole graph;
+// otherwise a rebuild scans the compact list of alive non-isolated vertices,
+// takes the exact maximum D, sets tau = D/2 and refills H.  No work per
+// decrement.  The rank-ordered alive list used for selection is compacted
+// separately when most of its live range is dead.
 //
 // Every adjacency pass is edge-balanced (lbs_for_each), so hub rows of
 // power-law graphs are split across many warps.
@@ -47,18 +47,20 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanU = 4;                    // alive-list entries per thread per scan step
-constexpr int32_t kAliveHi = 0x7FFFFFFF;
-constexpr uint32_t kUndecided = 0, kCenter = 1, kNonCenter = 2;
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
 constexpr int kRun = 0, kDone = 1, kRebuild = 2, kAbort = 3, kRebuildDelta = 4, kScanH = 5;
 constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
 
-__device__ __forceinline__ int32_t hi_of(unsigned long long x) { return (int32_t)(x >> 32); }
-__device__ __forceinline__ uint32_t lo_of(unsigned long long x) { return (uint32_t)x; }
-__device__ __forceinline__ int32_t decode_label(int32_t hi) { return hi < 0 ? ~hi : hi; }
-__device__ __forceinline__ unsigned long long word(int32_t hi, uint32_t lo) {
-  return ((unsigned long long)(uint32_t)hi << 32) | lo;
-}
+// State word of a vertex (uint32):
+//   alive ........... kAlive | residual degree
+//   clustered ....... kLab + center rank
+//   active this round kActive (undecided, or a ClusterWild! center),
+//                     kActCenter / kActNon (C4 center / non-center)
+constexpr uint32_t kAlive = 0x80000000u, kDegMask = 0x7FFFFFFFu, kLab = 16;
+constexpr uint32_t kActive = 1, kActCenter = 2, kActNon = 3;
+__device__ __forceinline__ bool is_alive(uint32_t x) { return x >= kAlive; }
+__device__ __forceinline__ uint32_t deg_of(uint32_t x) { return x & kDegMask; }
+__device__ __forceinline__ bool is_active(uint32_t x) { return x < kLab; }
 
 template <class T>
 __device__ __forceinline__ T vload(const T* p) { return *reinterpret_cast<const volatile T*>(p); }
@@ -356,8 +358,8 @@ struct K {
     if (S->dec) return;
     int64_t mx = -1;
     for (int64_t i = threadIdx.x; i < c.h_len; i += blockDim.x) {
-      const unsigned long long x = ldcg(B.st + ldcg(B.hv + i));
-      if (hi_of(x) == kAliveHi) mx = (int64_t)lo_of(x) > mx ? (int64_t)lo_of(x) : mx;
+      const uint32_t x = ldcg(B.st + ldcg(B.hv + i));
+      if (is_alive(x)) mx = (int64_t)deg_of(x) > mx ? (int64_t)deg_of(x) : mx;
     }
     mx = block_max<int64_t>(mx, S->scr);
     co_after_heavy((int32_t)mx);
@@ -430,7 +432,7 @@ struct K {
       }
 #pragma unroll
       for (int q = 0; q < kScanU; ++q)
-        cnt += (a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi) ? 1 : 0;
+        cnt += (a[q].y >= 0 && is_alive(ldcg(B.st + a[q].y))) ? 1 : 0;
     }
     cnt = block_sum<int64_t>(cnt, S->scr);
     if (threadIdx.x == 0) B.blk_a[bid] = cnt;
@@ -456,7 +458,7 @@ struct K {
       }
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
-        alive[q] = a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi;
+        alive[q] = a[q].y >= 0 && is_alive(ldcg(B.st + a[q].y));
         mine += alive[q] ? 1 : 0;
       }
       int64_t tot;
@@ -496,8 +498,8 @@ struct K {
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
         if (v[q] < 0) continue;
-        const unsigned long long x = ldcg(B.st + v[q]);
-        if (hi_of(x) == kAliveHi) mx = (int64_t)lo_of(x) > mx ? (int64_t)lo_of(x) : mx;
+        const uint32_t x = ldcg(B.st + v[q]);
+        if (is_alive(x)) mx = (int64_t)deg_of(x) > mx ? (int64_t)deg_of(x) : mx;
       }
     }
     mx = block_max<int64_t>(mx, S->scr);
@@ -534,10 +536,10 @@ struct K {
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
         if (v[q] < 0) continue;
-        const unsigned long long x = ldcg(B.st + v[q]);
-        if (hi_of(x) == kAliveHi && lo_of(x) > 0) {
+        const uint32_t x = ldcg(B.st + v[q]);
+        if (is_alive(x) && deg_of(x) > 0) {
           ++cnt;
-          mx = (int64_t)lo_of(x) > mx ? (int64_t)lo_of(x) : mx;
+          mx = (int64_t)deg_of(x) > mx ? (int64_t)deg_of(x) : mx;
         }
       }
     }
@@ -573,8 +575,8 @@ struct K {
       for (int q = 0; q < kScanU; ++q) {
         d[q] = 0;
         if (v[q] < 0) continue;
-        const unsigned long long x = ldcg(B.st + v[q]);
-        if (hi_of(x) == kAliveHi) d[q] = lo_of(x);
+        const uint32_t x = ldcg(B.st + v[q]);
+        if (is_alive(x)) d[q] = deg_of(x);
         mine += d[q] > 0 ? 1 : 0;
         heavy += (d[q] > 0 && (int64_t)d[q] >= tau) ? 1 : 0;
       }
@@ -633,15 +635,16 @@ struct K {
       row[q] = 0;
       if (!want[q]) continue;
       const int32_t r = a[q].x, v = a[q].y;
-      const uint32_t d = lo_of(ldcg(B.st + v));
+      const uint32_t d = deg_of(ldcg(B.st + v));
       B.size[r] = 0;
       if (d == 0) {                             // no alive neighbour: singleton center
-        B.st[v] = word(r, 0);
+        B.st[v] = kLab + (uint32_t)r;
         t.centers += 1;
       } else {
         row[q] = __ldg(B.off + v);
         deg0[q] = __ldg(B.off + v + 1) - row[q];
-        B.st[v] = word(~r, algo == kAlgoCW ? kCenter : kUndecided);
+        B.arank[v] = r;
+        B.st[v] = kActive;
         listed[q] = true;
         nl += 1;
         el += deg0[q];
@@ -681,6 +684,15 @@ struct K {
       const int64_t wlo = P().win_lo, wlen = P().win_len;
       int64_t s, e;
       slice(wlo, wlen, &s, &e);
+      // the previous round's centers still hold the active marker: give them
+      // their labels (own rank) before this round marks new actives
+      if (P().r0 < 0) {
+        const int64_t pn = P().act_n;
+        for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < pn; j += (int64_t)G * blockDim.x) {
+          const int32_t v = ldcg(B.act_v + j);
+          if (is_active(ldcg(B.st + v))) B.st[v] = kLab + (uint32_t)ldcg(B.act_r + j);
+        }
+      }
       // S1: alive count per block
       int64_t cnt = 0;
       for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
@@ -692,7 +704,7 @@ struct K {
         }
 #pragma unroll
         for (int q = 0; q < kScanU; ++q)
-          cnt += (a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi) ? 1 : 0;
+          cnt += (a[q].y >= 0 && is_alive(ldcg(B.st + a[q].y))) ? 1 : 0;
       }
       cnt = block_sum<int64_t>(cnt, S->scr);
       if (threadIdx.x == 0) B.blk_a[bid] = cnt;
@@ -720,7 +732,7 @@ struct K {
           }
 #pragma unroll
           for (int q = 0; q < kScanU; ++q) {
-            alive[q] = a[q].y >= 0 && hi_of(ldcg(B.st + a[q].y)) == kAliveHi;
+            alive[q] = a[q].y >= 0 && is_alive(ldcg(B.st + a[q].y));
             mine += alive[q] ? 1 : 0;
           }
           int64_t tot;
@@ -787,14 +799,13 @@ struct K {
   // ---------------- createCluster: push a center's rank to its neighbours ----
   // Lanes with push == true try to attach u (state word x, read earlier) to
   // the center of rank r.  All 32 lanes must call it.
-  __device__ void attach_one(bool push, int32_t u, int32_t r, unsigned long long x) {
+  __device__ void attach_one(bool push, int32_t u, int32_t r, uint32_t x) {
     bool fresh = false;
     uint32_t d_old = 0;
-    const unsigned long long nv = (unsigned long long)(uint32_t)r << 32;
-    if (push && (long long)x > (long long)nv) {
-      const unsigned long long old =
-          (unsigned long long)atomicMin(reinterpret_cast<long long*>(B.st + u), (long long)nv);
-      if (hi_of(old) == kAliveHi) { fresh = true; d_old = lo_of(old); }
+    const uint32_t nv = kLab + (uint32_t)r;
+    if (push && x > nv) {
+      const uint32_t old = atomicMin(B.st + u, nv);
+      if (is_alive(old)) { fresh = true; d_old = deg_of(old); }
     }
     if (fresh) t.attached += 1;
     // The center is the only alive neighbour of a fresh vertex of residual
@@ -820,7 +831,7 @@ struct K {
     lbs(B.act_e, an, aE, [&](const Lbs& L) {
       bool push[kLbsK];
       int32_t u[kLbsK];
-      unsigned long long x[kLbsK];
+      uint32_t x[kLbsK];
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         push[q] = L.ok(q) && (!skip_blocked || ldcg(B.blk_flag + L.item(q)) == 0);
@@ -837,7 +848,6 @@ struct K {
   // ---------------- C4: blocked detection ------------------------------------
   __device__ void c4_detect() {
     const int64_t an = P().act_n, aE = P().act_E;
-    const int32_t r0 = P().r0;
     lbs(B.act_e, an, aE, [&](const Lbs& L) {
       int32_t u[kLbsK];
 #pragma unroll
@@ -845,9 +855,8 @@ struct K {
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         if (!L.ok(q)) continue;
-        const int32_t hw = hi_of(ldcg(B.st + u[q]));
         // an earlier active neighbour: v must wait (isCenter)
-        if (hw < 0 && ~hw >= r0 && ~hw < L.vtx(q)) B.blk_flag[L.item(q)] = 1;
+        if (is_active(ldcg(B.st + u[q])) && ldcg(B.arank + u[q]) < L.vtx(q)) B.blk_flag[L.item(q)] = 1;
       }
     }, B.act_d, B.act_r);
   }
@@ -870,7 +879,8 @@ struct K {
           len = __ldg(B.off + v + 1) - __ldg(B.off + v);
           t.blocked += 1;
         } else {
-          B.st[v] = word(~r, kCenter);
+          B.st[v] = kActCenter;
+          (void)r;
           t.centers += 1;
         }
       }
@@ -892,21 +902,18 @@ struct K {
   // undecided blocked vertex.
   __device__ void c4_fix_scan() {
     const int64_t bn = P().b_n, bE = P().b_E;
-    const int32_t r0 = P().r0;
     lbs(B.b_e, bn, bE, [&](const Lbs& L) {
 #pragma unroll
       for (int i = 0; i < kLbsK; ++i) {
         if (!L.ok(i)) continue;
         const int32_t j = ldcg(B.b_j + L.item(i));
         const int32_t v = ldcg(B.act_v + j), rv = ldcg(B.act_r + j);
-        if (lo_of(ldcg(B.st + v)) != kUndecided) continue;
+        if (ldcg(B.st + v) != kActive) continue;
         const int32_t u = __ldg(B.col + L.edge(i) + ldcg(B.b_d + L.item(i)));
-        const unsigned long long x = ldcg(B.st + u);
-        const int32_t hw = hi_of(x);
-        if (hw < 0 && ~hw >= r0 && ~hw < rv) {
-          const uint32_t su = lo_of(x);
-          if (su == kCenter) B.hit_c[L.item(i)] = 1;
-          else if (su == kUndecided) B.hit_p[L.item(i)] = 1;
+        const uint32_t x = ldcg(B.st + u);
+        if (is_active(x) && ldcg(B.arank + u) < rv) {
+          if (x == kActCenter) B.hit_c[L.item(i)] = 1;
+          else if (x == kActive) B.hit_p[L.item(i)] = 1;
         }
       }
     });
@@ -919,9 +926,10 @@ struct K {
     for (int64_t q = bid * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
       const int32_t j = ldcg(B.b_j + q);
       const int32_t v = ldcg(B.act_v + j), r = ldcg(B.act_r + j);
-      if (lo_of(ldcg(B.st + v)) != kUndecided) continue;
-      if (ldcg(B.hit_c + q)) B.st[v] = word(~r, kNonCenter);
-      else if (!ldcg(B.hit_p + q)) { B.st[v] = word(~r, kCenter); t.centers += 1; }
+      (void)r;
+      if (ldcg(B.st + v) != kActive) continue;
+      if (ldcg(B.hit_c + q)) B.st[v] = kActNon;
+      else if (!ldcg(B.hit_p + q)) { B.st[v] = kActCenter; t.centers += 1; }
       else left += 1;
       B.hit_c[q] = 0;
       B.hit_p[q] = 0;
@@ -933,24 +941,22 @@ struct K {
   // lowest center rank among their neighbours.
   __device__ void c4_blocked_attach() {
     const int64_t bn = P().b_n, bE = P().b_E;
-    const int32_t r0 = P().r0;
     lbs(B.b_e, bn, bE, [&](const Lbs& L) {
 #pragma unroll
       for (int i = 0; i < kLbsK; ++i) {
         bool push = false;
         int32_t u = 0, r = 0;
-        unsigned long long x = 0;
+        uint32_t x = 0;
         if (L.ok(i)) {
           const int32_t j = ldcg(B.b_j + L.item(i));
           const int32_t v = ldcg(B.act_v + j);
           r = ldcg(B.act_r + j);
           u = __ldg(B.col + L.edge(i) + ldcg(B.b_d + L.item(i)));
           x = ldcg(B.st + u);
-          if (lo_of(ldcg(B.st + v)) == kCenter) {
+          if (ldcg(B.st + v) == kActCenter) {
             push = true;
-          } else {
-            const int32_t hw = hi_of(x);
-            if (hw < 0 && ~hw >= r0 && lo_of(x) == kCenter) atomicMin(B.pull + L.item(i), ~hw);
+          } else if (x == kActCenter) {
+            atomicMin(B.pull + L.item(i), ldcg(B.arank + u));
           }
         }
         attach_one(push, u, r, x);
@@ -973,10 +979,10 @@ struct K {
       if (q < bn) {
         const int32_t j = ldcg(B.b_j + q);
         v = ldcg(B.act_v + j);
-        if (lo_of(ldcg(B.st + v)) == kNonCenter) {
+        if (ldcg(B.st + v) == kActNon) {
           const int32_t lab = ldcg(B.pull + q);
           if (lab == 0x7FFFFFFF) fail(kErrInternal);   // a non-center always has a center neighbour
-          B.st[v] = word(lab, 0);
+          B.st[v] = kLab + (uint32_t)lab;
           t.noncenter += 1;
           row = ldcg(B.b_e + q) + ldcg(B.b_d + q);
           len = __ldg(B.off + v + 1) - __ldg(B.off + v);
@@ -992,12 +998,12 @@ struct K {
   __device__ void decrement() {
     const int64_t nn = P().new_n, nE = P().new_E;
     lbs(B.new_e, nn, nE, [&](const Lbs& L) {
-      int32_t w[kLbsK], lu[kLbsK];
-      unsigned long long x[kLbsK];
+      int32_t w[kLbsK];
+      uint32_t lu[kLbsK], x[kLbsK];
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         w[q] = L.ok(q) ? __ldg(B.col + L.csr(q)) : 0;
-        lu[q] = L.ok(q) ? hi_of(ldcg(B.st + L.vtx(q))) : 0;
+        lu[q] = L.ok(q) ? ldcg(B.st + L.vtx(q)) - kLab : 0;     // the member's (final) label
       }
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) x[q] = L.ok(q) ? ldcg(B.st + w[q]) : 0;
@@ -1005,11 +1011,12 @@ struct K {
       for (int q = 0; q < kLbsK; ++q) {
         if (!L.ok(q)) continue;
         if (L.in_row(q) == 0) atomicAdd(B.size + lu[q], 1);   // once per removed member
-        const int32_t hw = hi_of(x[q]);
-        if (hw == kAliveHi) {
-          atomicSub(reinterpret_cast<unsigned*>(B.st + w[q]), 1u);   // low word, result unused
-        } else if (decode_label(hw) == lu[q]) {
-          if (hw < 0) t.mc += 1; else t.mm += 1;
+        if (is_alive(x[q])) {
+          atomicSub(B.st + w[q], 1u);                          // result unused
+        } else if (is_active(x[q])) {                          // a center of this round
+          if ((uint32_t)ldcg(B.arank + w[q]) == lu[q]) t.mc += 1;
+        } else if (x[q] - kLab == lu[q]) {
+          t.mm += 1;
         }
       }
     }, B.new_d, B.new_v);
@@ -1160,7 +1167,7 @@ __device__ bool team_permutation(K& k, uint64_t seed) {
     const uint64_t key = perm_key(seed, (uint64_t)v);
     atomicAdd(&S.u.perm.hist[bits == 0 ? 0 : (int)(key >> (64 - bits))], 1);
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
-    B.st[v] = word(kAliveHi, (uint32_t)d);
+    B.st[v] = kAlive | (uint32_t)d;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
@@ -1313,8 +1320,9 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
     unsigned long long pairs = 0;
     int32_t* const lab = jobs[j].labels;
     for (int64_t v = (int64_t)k.bid * blockDim.x + threadIdx.x; v < rb.n; v += (int64_t)G * blockDim.x) {
-      const int32_t c = decode_label(hi_of(ldcg(rb.st + v)));
-      if (c < 0 || c >= rb.n) { k.fail(kErrInternal); continue; }
+      const uint32_t x = ldcg(rb.st + v);
+      const int64_t c = is_active(x) ? (int64_t)ldcg(rb.arank + v) : (int64_t)x - kLab;
+      if (is_alive(x) || c < 0 || c >= rb.n) { k.fail(kErrInternal); continue; }
       const int32_t cv = ldcg(rb.order + c);
       if (lab) lab[v] = cv;
       if (cv == v) {
@@ -1342,7 +1350,7 @@ __global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm) {
   const int64_t n = B.n;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
-    B.st[v] = word(kAliveHi, (uint32_t)d);
+    B.st[v] = kAlive | (uint32_t)d;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Ctl* C = B.ctl;
@@ -1361,9 +1369,9 @@ __global__ void k_finalize_labels(RoundBuffers B, int32_t* __restrict__ labels) 
   const int64_t n = B.n;
   unsigned long long pairs = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t hw = hi_of(B.st[v]);
-    const int32_t c = decode_label(hw);
-    if (hw == kAliveHi || c < 0 || c >= n) {
+    const uint32_t x = B.st[v];
+    const int64_t c = is_active(x) ? (int64_t)B.arank[v] : (int64_t)x - kLab;   // last round's centers
+    if (is_alive(x) || c < 0 || c >= n) {
       atomicCAS(&B.ctl->err, kOk, kErrInternal);
       if (labels) labels[v] = -1;
       continue;
@@ -1385,7 +1393,8 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   const size_t nn = (size_t)(n > 0 ? n : 1);
   size_t b = 0;
   b += align_up(sizeof(Ctl));
-  b += align_up(8 * nn);                 // st
+  b += align_up(4 * nn);                 // st
+  b += align_up(4 * nn);                 // arank
   b += 2 * align_up(8 * nn);             // al0, al1
   b += 2 * align_up(4 * nn) + 2 * align_up(8 * nn);   // act_v, act_r, act_e, act_d
   b += align_up(4 * nn) + 2 * align_up(8 * nn);       // new_v, new_e, new_d
@@ -1403,7 +1412,8 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   char* p = static_cast<char*>(ws);
   auto take = [&](size_t bytes) { char* q = p; p += align_up(bytes); return q; };
   B->ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
-  B->st = reinterpret_cast<unsigned long long*>(take(8 * nn));
+  B->st = reinterpret_cast<uint32_t*>(take(4 * nn));
+  B->arank = reinterpret_cast<int32_t*>(take(4 * nn));
   B->al0 = reinterpret_cast<int2*>(take(8 * nn));
   B->al1 = reinterpret_cast<int2*>(take(8 * nn));
   B->act_v = reinterpret_cast<int32_t*>(take(4 * nn));
