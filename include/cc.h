@@ -82,6 +82,8 @@ typedef struct cc_round_stats {
   int64_t removed;   /* vertices clustered this round (A_i included)          */
   int64_t blocked;   /* C4: actives with an earlier-ranked active neighbour   */
   int64_t edges;     /* adjacency entries read by this round's passes         */
+  int64_t ns;        /* device time of the round (from the previous round's end,
+                        its Delta work included), nanoseconds                 */
 } cc_round_stats;
 
 /*

@@ -255,95 +255,102 @@ __device__ __forceinline__ int64_t warp_upper_bound(const int64_t* a, int64_t n,
   return lo + __popc(__ballot_sync(FULL, le));
 }
 
+// One chunk [c0, cend) of the walk: find the item holding c0, then batches
+// of kLbsW virtual edges.
+template <class F>
+__device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, int64_t c0, int64_t cend, LbsWarp* ws,
+                                          F& f, const int64_t* delta, const int32_t* vtx) {
+  const int lane = threadIdx.x & 31;
+  int64_t j0 = warp_upper_bound(epos, nitems, c0) - 1;
+  for (int64_t base = c0; base < cend; base += kLbsW) {
+    int64_t s[kLbsK];
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      const int64_t jj = j0 + lane + 32 * t;
+      const bool in = jj < nitems;
+      s[t] = in ? ldcg(epos + jj) : INT64_MAX;
+      // per-item data loads issue together with the start offsets
+      if (delta) ws->dlt[lane + 32 * t] = in ? ldcg(delta + jj) : 0;
+      if (vtx) ws->vtx[lane + 32 * t] = in ? ldcg(vtx + jj) : 0;
+      ws->mark[lane + 32 * t] = -1;
+    }
+    if (lane == 0) ws->next = -1;
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      const int i = lane + 32 * t;
+      if (s[t] < base + kLbsW) {
+        ws->rel[i] = (int32_t)(s[t] - base);
+        if (s[t] >= base) ws->mark[s[t] - base] = i;
+      } else if (s[t] == base + kLbsW) {
+        ws->next = i;                  // the item that starts the next batch
+      }
+    }
+    __syncwarp();
+    // segmented max-scan: each position takes the last item starting at or before it
+    int v[kLbsK];
+    int run = -1;
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      const int m = ws->mark[lane * kLbsK + t];
+      run = m > run ? m : run;
+      v[t] = run;
+    }
+    int inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(FULL, inc, o);
+      if (lane >= o) inc = y > inc ? y : inc;
+    }
+    int exc = __shfl_up_sync(FULL, inc, 1);
+    if (lane == 0) exc = -1;
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      int m = v[t] > exc ? v[t] : exc;
+      ws->mark[lane * kLbsK + t] = m < 0 ? 0 : m;
+    }
+    __syncwarp();
+    Lbs L;
+    L.j0 = j0;
+    L.base = base;
+    L.ws = ws;
+    L.valid = 0;
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      const int p = lane + 32 * t;
+      L.ri[t] = ws->mark[p];
+      if (base + p < cend) L.valid |= 1u << t;
+    }
+    const int last = ws->mark[kLbsW - 1];
+    const int nxt = ws->next;
+    f(L);
+    __syncwarp();
+    // next batch: the item holding its first edge is the last item of this
+    // batch or, when an item starts exactly at the next base, that item (the
+    // item after `last` is always among the ones loaded here unless `last`
+    // is the final loaded slot, in which case one load decides)
+    if (nxt >= 0) j0 += nxt;
+    else if (last == kLbsW - 1 && j0 + kLbsW < nitems && ldcg(epos + j0 + kLbsW) <= base + kLbsW) j0 += kLbsW;
+    else j0 += last;
+  }
+}
+
 // gwarp / nwarps: this warp's index among, and the number of, the warps that
-// share the walk (the whole grid, or one team of blocks).
+// share the walk (the whole grid, or one team of blocks).  Warp w takes
+// chunks w, w + nwarps, ...
 template <class F>
 __device__ __forceinline__ void lbs_for_each_in(int64_t gwarp, int64_t nwarps, const int64_t* epos, int64_t nitems,
                                                 int64_t E, LbsWarp* ws, F&& f, const int64_t* delta = nullptr,
                                                 const int32_t* vtx = nullptr) {
   if (E <= 0) return;
-  const int lane = threadIdx.x & 31;
   // up to kLbsBatches batches per chunk, fewer when the list is short, so
   // that short lists still spread over many warps
   int64_t nb = E / (nwarps * (int64_t)kLbsW * 2);
   nb = nb < 1 ? 1 : (nb > kLbsBatches ? kLbsBatches : nb);
   const int64_t kChunk = (int64_t)kLbsW * nb;
-  for (int64_t c0 = gwarp * kChunk; c0 < E; c0 += nwarps * kChunk) {
-    int64_t j0 = warp_upper_bound(epos, nitems, c0) - 1;
-    const int64_t cend = c0 + kChunk < E ? c0 + kChunk : E;
-    for (int64_t base = c0; base < cend; base += kLbsW) {
-      int64_t s[kLbsK];
-#pragma unroll
-      for (int t = 0; t < kLbsK; ++t) {
-        const int64_t jj = j0 + lane + 32 * t;
-        const bool in = jj < nitems;
-        s[t] = in ? ldcg(epos + jj) : INT64_MAX;
-        // per-item data loads issue together with the start offsets
-        if (delta) ws->dlt[lane + 32 * t] = in ? ldcg(delta + jj) : 0;
-        if (vtx) ws->vtx[lane + 32 * t] = in ? ldcg(vtx + jj) : 0;
-        ws->mark[lane + 32 * t] = -1;
-      }
-      if (lane == 0) ws->next = -1;
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < kLbsK; ++t) {
-        const int i = lane + 32 * t;
-        if (s[t] < base + kLbsW) {
-          ws->rel[i] = (int32_t)(s[t] - base);
-          if (s[t] >= base) ws->mark[s[t] - base] = i;
-        } else if (s[t] == base + kLbsW) {
-          ws->next = i;                  // the item that starts the next batch
-        }
-      }
-      __syncwarp();
-      // segmented max-scan: each position takes the last item starting at or before it
-      int v[kLbsK];
-      int run = -1;
-#pragma unroll
-      for (int t = 0; t < kLbsK; ++t) {
-        const int m = ws->mark[lane * kLbsK + t];
-        run = m > run ? m : run;
-        v[t] = run;
-      }
-      int inc = run;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc = y > inc ? y : inc;
-      }
-      int exc = __shfl_up_sync(FULL, inc, 1);
-      if (lane == 0) exc = -1;
-      __syncwarp();
-#pragma unroll
-      for (int t = 0; t < kLbsK; ++t) {
-        int m = v[t] > exc ? v[t] : exc;
-        ws->mark[lane * kLbsK + t] = m < 0 ? 0 : m;
-      }
-      __syncwarp();
-      Lbs L;
-      L.j0 = j0;
-      L.base = base;
-      L.ws = ws;
-      L.valid = 0;
-#pragma unroll
-      for (int t = 0; t < kLbsK; ++t) {
-        const int p = lane + 32 * t;
-        L.ri[t] = ws->mark[p];
-        if (base + p < cend) L.valid |= 1u << t;
-      }
-      const int last = ws->mark[kLbsW - 1];
-      const int nxt = ws->next;
-      f(L);
-      __syncwarp();
-      // next batch: the item holding its first edge is the last item of this
-      // batch or, when an item starts exactly at the next base, that item (the
-      // item after `last` is always among the ones loaded here unless `last`
-      // is the final loaded slot, in which case one load decides)
-      if (nxt >= 0) j0 += nxt;
-      else if (last == kLbsW - 1 && j0 + kLbsW < nitems && ldcg(epos + j0 + kLbsW) <= base + kLbsW) j0 += kLbsW;
-      else j0 += last;
-    }
-  }
+  for (int64_t c0 = gwarp * kChunk; c0 < E; c0 += nwarps * kChunk)
+    lbs_chunk(epos, nitems, c0, c0 + kChunk < E ? c0 + kChunk : E, ws, f, delta, vtx);
 }
 
 template <class F>

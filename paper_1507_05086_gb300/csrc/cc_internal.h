@@ -20,7 +20,7 @@ cudaError_t launch_permutation(int64_t n, uint64_t seed, int32_t* order, void* w
 // ---- rounds (cc_rounds.cu) ---------------------------------------------------
 // Per-round statistics as written by the device (layout of cc_round_stats).
 struct RoundStat {
-  int64_t n_alive, delta, k, centers, removed, blocked, edges;
+  int64_t n_alive, delta, k, centers, removed, blocked, edges, ns;
 };
 
 // Plan of the next phase, published by the coordinator block at every grid

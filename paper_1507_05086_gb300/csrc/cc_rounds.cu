@@ -77,7 +77,7 @@ struct Coord {
   int32_t tau, delta, max_deg, d_new;
   int algo, al_sel, al_ident, rebuilds_in_row;
   int nz_sel, nz_static;
-  unsigned long long t0;
+  unsigned long long t0, round_t0;
   unsigned long long ph_ns[8];
 };
 
@@ -403,8 +403,10 @@ struct K {
         RoundStat s;
         s.n_alive = c.n_alive; s.delta = c.delta; s.k = k; s.centers = centers;
         s.removed = removed; s.blocked = blocked; s.edges = c.r_edges + (int64_t)(np & kPackEdgeMask);
+        s.ns = (int64_t)(globaltimer_ns() - c.round_t0);
         B.stats[r] = s;
       }
+      c.round_t0 = globaltimer_ns();
       if (centers_seen != centers) fail(kErrInternal);
       c.n_alive -= removed;
       if (c.n_alive < 0) fail(kErrInternal);
@@ -1044,6 +1046,7 @@ __device__ void run_job(K& k, int algo) {
   if (k.bid == 0 && threadIdx.x == 0) {
     for (int i = 0; i < 8; ++i) S.co.ph_ns[i] = 0;
     S.co.t0 = globaltimer_ns();
+    S.co.round_t0 = S.co.t0;
   }
   __syncthreads();
   if (!k.sync(7, [&] { k.co_init(); })) goto out;

@@ -28,7 +28,7 @@ STATUS = {
     -5: "device wait timed out", -6: "busy", -7: "internal consistency check failed",
 }
 
-ROUND_STAT_FIELDS = ("n_alive", "delta", "k", "centers", "removed", "blocked", "edges")
+ROUND_STAT_FIELDS = ("n_alive", "delta", "k", "centers", "removed", "blocked", "edges", "ns")
 
 
 class RoundStats(ctypes.Structure):

@@ -119,6 +119,12 @@ def test_invariants_and_round_structure_on_gpu_output(cc, ora, gg):
             _, _, ar, _ = ora.rounds(g.off, g.col, order, a, 0.5, 1, want_active_round=True)
             chk.check_round_structure(g.off, g.col, order, lab, ar, st, 500_000, a, ora.batch_size)
             chk.check_min_rank_center(g.off, g.col, order, lab, ar, a)
+            # every round took some device time, and no round took longer than the kernel
+            graph.set_timing(True)
+            _, _, _, st = graph.cluster(algo, 0.5, 77, stats_cap=100_000)
+            assert (st["ns"] > 0).all()
+            assert st["ns"].sum() <= graph.last_timings()[1] * 1e6 * 1.01 + 1e5
+            graph.set_timing(False)
 
 
 def test_disagreements_of_arbitrary_labels(cc, ora, gg):
