@@ -256,13 +256,42 @@ __device__ __forceinline__ int64_t warp_upper_bound(const int64_t* a, int64_t n,
 }
 
 // One chunk [c0, cend) of the walk: find the item holding c0, then batches
-// of kLbsW virtual edges.
+// of kLbsW virtual edges.  A batch that lies inside one item (a long row)
+// needs none of the per-item loads: the warp keeps the range, delta and
+// vertex of its current item, taken from the previous batch's loads, and
+// only a batch that crosses an item boundary loads and scans item starts.
 template <class F>
 __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, int64_t c0, int64_t cend, LbsWarp* ws,
                                           F& f, const int64_t* delta, const int32_t* vtx) {
   const int lane = threadIdx.x & 31;
   int64_t j0 = warp_upper_bound(epos, nitems, c0) - 1;
+  // cached item (warp-uniform): valid when cur_j == j0
+  int64_t cur_j = -1, cur_start = 0, cur_end = 0, cur_dlt = 0;
+  int32_t cur_vtx = 0;
   for (int64_t base = c0; base < cend; base += kLbsW) {
+    Lbs L;
+    L.j0 = j0;
+    L.base = base;
+    L.ws = ws;
+    L.valid = 0;
+    if (cur_j == j0 && cur_end >= base + kLbsW) {
+      // the whole batch belongs to item j0
+      if (lane == 0) {
+        ws->rel[0] = (int32_t)(cur_start - base);
+        ws->dlt[0] = cur_dlt;
+        ws->vtx[0] = cur_vtx;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int t = 0; t < kLbsK; ++t) {
+        L.ri[t] = 0;
+        if (base + lane + 32 * t < cend) L.valid |= 1u << t;
+      }
+      f(L);
+      __syncwarp();
+      if (cur_end == base + kLbsW) ++j0;          // the next batch starts the next item
+      continue;
+    }
     int64_t s[kLbsK];
 #pragma unroll
     for (int t = 0; t < kLbsK; ++t) {
@@ -279,8 +308,11 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
 #pragma unroll
     for (int t = 0; t < kLbsK; ++t) {
       const int i = lane + 32 * t;
+      // start relative to the batch, clamped to int32 (items past the end of
+      // the list, or starting 2^31 edges later, read as INT32_MAX)
+      const int64_t r = s[t] - base;
+      ws->rel[i] = s[t] == INT64_MAX || r > INT32_MAX - 1 ? INT32_MAX : (int32_t)r;
       if (s[t] < base + kLbsW) {
-        ws->rel[i] = (int32_t)(s[t] - base);
         if (s[t] >= base) ws->mark[s[t] - base] = i;
       } else if (s[t] == base + kLbsW) {
         ws->next = i;                  // the item that starts the next batch
@@ -311,11 +343,6 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
       ws->mark[lane * kLbsK + t] = m < 0 ? 0 : m;
     }
     __syncwarp();
-    Lbs L;
-    L.j0 = j0;
-    L.base = base;
-    L.ws = ws;
-    L.valid = 0;
 #pragma unroll
     for (int t = 0; t < kLbsK; ++t) {
       const int p = lane + 32 * t;
@@ -324,15 +351,24 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
     }
     const int last = ws->mark[kLbsW - 1];
     const int nxt = ws->next;
-    f(L);
-    __syncwarp();
     // next batch: the item holding its first edge is the last item of this
     // batch or, when an item starts exactly at the next base, that item (the
     // item after `last` is always among the ones loaded here unless `last`
     // is the final loaded slot, in which case one load decides)
-    if (nxt >= 0) j0 += nxt;
-    else if (last == kLbsW - 1 && j0 + kLbsW < nitems && ldcg(epos + j0 + kLbsW) <= base + kLbsW) j0 += kLbsW;
-    else j0 += last;
+    int m = nxt >= 0 ? nxt : last;
+    if (nxt < 0 && last == kLbsW - 1 && j0 + kLbsW < nitems && ldcg(epos + j0 + kLbsW) <= base + kLbsW) m = kLbsW;
+    // remember the next batch's item when its range is among the loaded ones
+    if (m + 1 < kLbsW) {
+      const int32_t r1 = ws->rel[m + 1];
+      cur_j = j0 + m;
+      cur_start = base + ws->rel[m];
+      cur_end = r1 == INT32_MAX ? INT64_MAX : base + r1;
+      cur_dlt = delta ? ws->dlt[m] : 0;
+      cur_vtx = vtx ? ws->vtx[m] : 0;
+    }
+    f(L);
+    __syncwarp();
+    j0 += m;
   }
 }
 

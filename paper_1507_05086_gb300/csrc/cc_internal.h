@@ -30,7 +30,7 @@ struct Plan {
   int64_t take, act_n, act_E, new_n;
   int64_t new_E, b_n, b_E, undecided;
   int32_t th, r0, al_sel, al_ident;
-  int32_t state, pad0, pad1, pad2;
+  int32_t state, pad0, tag, pad2;      // tag: removal tag of the current round
 };
 static_assert(sizeof(Plan) == 128, "plan layout");
 
@@ -68,6 +68,7 @@ struct RoundBuffers {
   const int32_t* col;
   const int32_t* order;
   uint32_t* st;                // per-vertex state word
+  uint32_t* rtag;              // per-vertex removal tag, 4 bits (8 vertices per word)
   int32_t* arank;              // rank of a vertex while it is active
   int2* al0;                   // alive lists: (rank, vertex), rank-ordered
   int2* al1;

@@ -23,9 +23,13 @@
 // clustered and active vertices.
 //
 // Residual degrees live in the alive word itself, so the decrement that
-// follows the removal of a vertex is a fire-and-forget atomic on the word the
-// alive test just read; half the footprint of a label/degree pair keeps more
-// of the randomly accessed state in L2.  Delta_i (max residual degree, exact
+// follows the removal of a vertex is a fire-and-forget atomic on that word.
+// The alive tests of the hot passes read a separate removal tag instead:
+// 4 bits per vertex, 0 while alive, else 1 + (removal round mod 15), an
+// eighth of the state words' footprint, so the random reads of the edge
+// passes and of the selection scans mostly hit L2.  A tag equal to the
+// current round's only says "maybe removed this round" (a vertex removed
+// 15, 30, ... rounds earlier carries it too); the state word decides.  Delta_i (max residual degree, exact
 // every round) comes from a heavy list H: every alive vertex whose degree was
 // >= tau when H was built.  Degrees only fall, so if the largest current
 // degree in H is still >= tau it is the maximum over the whole graph;
@@ -58,9 +62,18 @@ constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are 
 //                     kActCenter / kActNon (C4 center / non-center)
 constexpr uint32_t kAlive = 0x80000000u, kDegMask = 0x7FFFFFFFu, kLab = 16;
 constexpr uint32_t kActive = 1, kActCenter = 2, kActNon = 3;
+constexpr int kTagCycle = 15;                // removal tags 1..15
 __device__ __forceinline__ bool is_alive(uint32_t x) { return x >= kAlive; }
 __device__ __forceinline__ uint32_t deg_of(uint32_t x) { return x & kDegMask; }
 __device__ __forceinline__ bool is_active(uint32_t x) { return x < kLab; }
+
+__device__ __forceinline__ int64_t rtag_words(int64_t n) { return (n >> 3) + 1; }
+__device__ __forceinline__ uint32_t rtag_of(const uint32_t* rtag, int32_t v) {
+  return (ldcg(rtag + (v >> 3)) >> ((v & 7) * 4)) & 15u;
+}
+__device__ __forceinline__ void set_rtag(uint32_t* rtag, int32_t v, uint32_t tag) {
+  atomicOr(rtag + (v >> 3), tag << ((v & 7) * 4));      // result unused
+}
 
 template <class T>
 __device__ __forceinline__ T vload(const T* p) { return *reinterpret_cast<const volatile T*>(p); }
@@ -322,6 +335,7 @@ struct K {
       p.win_len = c.win_len;
       p.th = 0;
       p.r0 = -1;
+      p.tag = (int32_t)(c.round % kTagCycle) + 1;
       p.al_sel = c.al_sel;
       p.al_ident = c.al_ident;
     }
@@ -434,7 +448,7 @@ struct K {
       }
 #pragma unroll
       for (int q = 0; q < kScanU; ++q)
-        cnt += (a[q].y >= 0 && is_alive(ldcg(B.st + a[q].y))) ? 1 : 0;
+        cnt += (a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0) ? 1 : 0;
     }
     cnt = block_sum<int64_t>(cnt, S->scr);
     if (threadIdx.x == 0) B.blk_a[bid] = cnt;
@@ -460,7 +474,7 @@ struct K {
       }
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
-        alive[q] = a[q].y >= 0 && is_alive(ldcg(B.st + a[q].y));
+        alive[q] = a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0;
         mine += alive[q] ? 1 : 0;
       }
       int64_t tot;
@@ -638,6 +652,7 @@ struct K {
       if (!want[q]) continue;
       const int32_t r = a[q].x, v = a[q].y;
       const uint32_t d = deg_of(ldcg(B.st + v));
+      set_rtag(B.rtag, v, (uint32_t)P().tag);
       B.size[r] = 0;
       if (d == 0) {                             // no alive neighbour: singleton center
         B.st[v] = kLab + (uint32_t)r;
@@ -706,7 +721,7 @@ struct K {
         }
 #pragma unroll
         for (int q = 0; q < kScanU; ++q)
-          cnt += (a[q].y >= 0 && is_alive(ldcg(B.st + a[q].y))) ? 1 : 0;
+          cnt += (a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0) ? 1 : 0;
       }
       cnt = block_sum<int64_t>(cnt, S->scr);
       if (threadIdx.x == 0) B.blk_a[bid] = cnt;
@@ -734,7 +749,7 @@ struct K {
           }
 #pragma unroll
           for (int q = 0; q < kScanU; ++q) {
-            alive[q] = a[q].y >= 0 && is_alive(ldcg(B.st + a[q].y));
+            alive[q] = a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0;
             mine += alive[q] ? 1 : 0;
           }
           int64_t tot;
@@ -807,7 +822,11 @@ struct K {
     const uint32_t nv = kLab + (uint32_t)r;
     if (push && x > nv) {
       const uint32_t old = atomicMin(B.st + u, nv);
-      if (is_alive(old)) { fresh = true; d_old = deg_of(old); }
+      if (is_alive(old)) {
+        fresh = true;
+        d_old = deg_of(old);
+        set_rtag(B.rtag, u, (uint32_t)P().tag);
+      }
     }
     if (fresh) t.attached += 1;
     // The center is the only alive neighbour of a fresh vertex of residual
@@ -839,8 +858,14 @@ struct K {
         push[q] = L.ok(q) && (!skip_blocked || ldcg(B.blk_flag + L.item(q)) == 0);
         u[q] = push[q] ? __ldg(B.col + L.csr(q)) : 0;
       }
+      // alive (tag 0): try the atomicMin directly; tagged this round (or 15k
+      // rounds ago): the state word decides; removed earlier: nothing to do
+      uint32_t tg[kLbsK];
 #pragma unroll
-      for (int q = 0; q < kLbsK; ++q) x[q] = push[q] ? ldcg(B.st + u[q]) : 0;
+      for (int q = 0; q < kLbsK; ++q) tg[q] = push[q] ? rtag_of(B.rtag, u[q]) : 16u;
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q)
+        x[q] = tg[q] == 0 ? 0xFFFFFFFFu : (tg[q] == (uint32_t)P().tag ? ldcg(B.st + u[q]) : 0u);
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) attach_one(push[q], u[q], L.vtx(q), x[q]);
     }, B.act_d, B.act_r);
@@ -857,7 +882,9 @@ struct K {
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         if (!L.ok(q)) continue;
-        // an earlier active neighbour: v must wait (isCenter)
+        // an earlier active neighbour: v must wait (isCenter); actives carry
+        // this round's tag
+        if (rtag_of(B.rtag, u[q]) != (uint32_t)P().tag) continue;
         if (is_active(ldcg(B.st + u[q])) && ldcg(B.arank + u[q]) < L.vtx(q)) B.blk_flag[L.item(q)] = 1;
       }
     }, B.act_d, B.act_r);
@@ -912,6 +939,7 @@ struct K {
         const int32_t v = ldcg(B.act_v + j), rv = ldcg(B.act_r + j);
         if (ldcg(B.st + v) != kActive) continue;
         const int32_t u = __ldg(B.col + L.edge(i) + ldcg(B.b_d + L.item(i)));
+        if (rtag_of(B.rtag, u) != (uint32_t)P().tag) continue;     // not an active of this round
         const uint32_t x = ldcg(B.st + u);
         if (is_active(x) && ldcg(B.arank + u) < rv) {
           if (x == kActCenter) B.hit_c[L.item(i)] = 1;
@@ -1007,14 +1035,22 @@ struct K {
         w[q] = L.ok(q) ? __ldg(B.col + L.csr(q)) : 0;
         lu[q] = L.ok(q) ? ldcg(B.st + L.vtx(q)) - kLab : 0;     // the member's (final) label
       }
+      uint32_t tg[kLbsK];
 #pragma unroll
-      for (int q = 0; q < kLbsK; ++q) x[q] = L.ok(q) ? ldcg(B.st + w[q]) : 0;
+      for (int q = 0; q < kLbsK; ++q) tg[q] = L.ok(q) ? rtag_of(B.rtag, w[q]) : 16u;
+      // alive: decrement; maybe removed this round: the state word decides
+      // whether w shares the member's cluster; removed earlier: nothing
+      const uint32_t tag = (uint32_t)P().tag;
+#pragma unroll
+      for (int q = 0; q < kLbsK; ++q) x[q] = tg[q] == tag ? ldcg(B.st + w[q]) : 0;
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         if (!L.ok(q)) continue;
         if (L.in_row(q) == 0) atomicAdd(B.size + lu[q], 1);   // once per removed member
-        if (is_alive(x[q])) {
+        if (tg[q] == 0) {
           atomicSub(B.st + w[q], 1u);                          // result unused
+        } else if (tg[q] != tag) {
+          continue;
         } else if (is_active(x[q])) {                          // a center of this round
           if ((uint32_t)ldcg(B.arank + w[q]) == lu[q]) t.mc += 1;
         } else if (x[q] - kLab == lu[q]) {
@@ -1172,6 +1208,7 @@ __device__ bool team_permutation(K& k, uint64_t seed) {
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
     B.st[v] = kAlive | (uint32_t)d;
   }
+  for (int64_t i = tid; i < rtag_words(n); i += nthr) B.rtag[i] = 0;
   __syncthreads();
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     const int h = S.u.perm.hist[i];
@@ -1355,6 +1392,8 @@ __global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm) {
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
     B.st[v] = kAlive | (uint32_t)d;
   }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rtag_words(n); i += (int64_t)gridDim.x * blockDim.x)
+    B.rtag[i] = 0;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     Ctl* C = B.ctl;
     C->algo = algo;
@@ -1397,6 +1436,7 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   size_t b = 0;
   b += align_up(sizeof(Ctl));
   b += align_up(4 * nn);                 // st
+  b += align_up(4 * ((nn >> 3) + 1));    // rtag
   b += align_up(4 * nn);                 // arank
   b += 2 * align_up(8 * nn);             // al0, al1
   b += 2 * align_up(4 * nn) + 2 * align_up(8 * nn);   // act_v, act_r, act_e, act_d
@@ -1416,6 +1456,7 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   auto take = [&](size_t bytes) { char* q = p; p += align_up(bytes); return q; };
   B->ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));
   B->st = reinterpret_cast<uint32_t*>(take(4 * nn));
+  B->rtag = reinterpret_cast<uint32_t*>(take(4 * ((nn >> 3) + 1)));
   B->arank = reinterpret_cast<int32_t*>(take(4 * nn));
   B->al0 = reinterpret_cast<int2*>(take(8 * nn));
   B->al1 = reinterpret_cast<int2*>(take(8 * nn));
