@@ -50,65 +50,9 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
-// ---------------------------------------------------------------------------
-// Grid barrier for a cooperative (co-resident) launch.  The last block to
-// arrive may run a "leader" step with the whole block before releasing the
-// others.  Every wait is bounded: after kBarrierLimitNs the waiter records
-// kErrTimeout in *err and returns false, and the kernel unwinds.
-// ---------------------------------------------------------------------------
+// Every spin-wait of the kernels is bounded: after kBarrierLimitNs the waiter
+// records kErrTimeout in the error word and the kernel unwinds.
 constexpr uint64_t kBarrierLimitNs = 4000000000ull;   // 4 s
-
-struct GridBarrier {
-  unsigned count;
-  unsigned gen;
-};
-
-// Phase 1: arrive.  Returns true in every thread of the block that arrived
-// last.  *gen_out (shared) receives the generation to wait on.
-__device__ __forceinline__ bool bar_arrive(GridBarrier* b, unsigned nblocks, unsigned* s_gen,
-                                           int* s_leader) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned g = ld_acquire(&b->gen);
-    __threadfence();
-    unsigned t = atomicAdd(&b->count, 1u);
-    *s_gen = g;
-    *s_leader = (t == nblocks - 1) ? 1 : 0;
-  }
-  __syncthreads();
-  return *s_leader != 0;
-}
-
-// Phase 2: the leader releases; everyone else waits (bounded).
-__device__ __forceinline__ bool bar_finish(GridBarrier* b, bool leader, unsigned* s_gen, int* err,
-                                           int* s_ok) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    if (leader) {
-      b->count = 0;
-      __threadfence();
-      st_release(&b->gen, *s_gen + 1);
-    } else {
-      uint64_t t0 = globaltimer_ns();
-      unsigned spins = 0;
-      while (ld_acquire(&b->gen) == *s_gen) {
-        if (ld_volatile_int(err) != kOk) { ok = 0; break; }
-        if (++spins > 64) __nanosleep(128);
-        if ((spins & 255) == 0 && globaltimer_ns() - t0 > kBarrierLimitNs) {
-          atomicCAS(err, kOk, kErrTimeout);
-          ok = 0;
-          break;
-        }
-      }
-      __threadfence();
-    }
-    if (ld_volatile_int(err) != kOk) ok = 0;
-    *s_ok = ok;
-  }
-  __syncthreads();
-  return *s_ok != 0;
-}
 
 // ---------------------------------------------------------------------------
 // Scans

@@ -33,6 +33,7 @@ struct Plan {
   int32_t state, pad0, tag, pad2;      // tag: removal tag of the current round
 };
 static_assert(sizeof(Plan) == 128, "plan layout");
+static_assert(offsetof(Plan, state) == 112, "the state word opens the last 16 bytes of the plan");
 
 // Device control block of one clustering job.  Zeroed by the host before
 // each launch; written by the kernels only.

@@ -199,6 +199,7 @@ struct K {
       __syncthreads();
       if (S->ok) act();
       __syncthreads();
+      // an error (here or in any block) travels in the plan as the abort state
       if (threadIdx.x == 0 && (!S->ok || ld_volatile_int(&C->err) != kOk)) S->plan.state = kAbort;
       __syncthreads();
       // publish: 128 bytes as eight 16-byte stores, then release
@@ -210,18 +211,27 @@ struct K {
       if (threadIdx.x == 0) {
         const uint64_t t0 = globaltimer_ns();
         unsigned spins = 0;
+        int released = 1;
         while (ld_acquire(&C->gen) < epoch) {
           if ((++spins & 63) == 0) {
-            if (ld_volatile_int(&C->err) != kOk) break;
-            if (globaltimer_ns() - t0 > kBarrierLimitNs) { atomicCAS(&C->err, kOk, kErrTimeout); break; }
+            if (ld_volatile_int(&C->err) != kOk) { released = 0; break; }
+            if (globaltimer_ns() - t0 > kBarrierLimitNs) {
+              atomicCAS(&C->err, kOk, kErrTimeout);
+              released = 0;
+              break;
+            }
           }
         }
+        S->ok = released;
       }
       __syncthreads();
-      if (threadIdx.x < sizeof(Plan) / 16)
-        reinterpret_cast<int4*>(&S->plan)[threadIdx.x] = __ldcg(reinterpret_cast<const int4*>(&C->plan) + threadIdx.x);
-      __syncthreads();
-      if (threadIdx.x == 0 && ld_volatile_int(&C->err) != kOk) S->plan.state = kAbort;
+      // the plan (its last 16 bytes hold the state word; without a release
+      // the copy is stale and the state becomes the abort state)
+      if (threadIdx.x < sizeof(Plan) / 16) {
+        int4 q = __ldcg(reinterpret_cast<const int4*>(&C->plan) + threadIdx.x);
+        if (threadIdx.x == sizeof(Plan) / 16 - 1 && !S->ok) q.x = kAbort;
+        reinterpret_cast<int4*>(&S->plan)[threadIdx.x] = q;
+      }
       __syncthreads();
     }
     return S->plan.state != kAbort;
@@ -263,15 +273,6 @@ struct K {
     }
     __syncthreads();
     return run;
-  }
-
-  __device__ int64_t max_blocks() {
-    int64_t m = 0;
-    for (unsigned b = threadIdx.x; b < G; b += blockDim.x) {
-      const int64_t x = ldcg(B.blk_b + b);
-      m = x > m ? x : m;
-    }
-    return block_max<int64_t>(m, S->scr);
   }
 
   // ---------------- coordinator actions ----------------------------------------
@@ -370,10 +371,22 @@ struct K {
     __syncthreads();
     if (S->dec == 2) { plan_selection(0); return; }
     if (S->dec) return;
+    // the whole block reads the heavy list, eight entries per thread at a time
+    // so that the dependent loads overlap
     int64_t mx = -1;
-    for (int64_t i = threadIdx.x; i < c.h_len; i += blockDim.x) {
-      const uint32_t x = ldcg(B.st + ldcg(B.hv + i));
-      if (is_alive(x)) mx = (int64_t)deg_of(x) > mx ? (int64_t)deg_of(x) : mx;
+    for (int64_t base = 0; base < c.h_len; base += 8 * (int64_t)blockDim.x) {
+      int32_t h[8];
+      uint32_t x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t i = base + threadIdx.x + (int64_t)q * blockDim.x;
+        h[q] = i < c.h_len ? ldcg(B.hv + i) : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = h[q] >= 0 ? ldcg(B.st + h[q]) : 0u;
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        if (is_alive(x[q])) mx = (int64_t)deg_of(x[q]) > mx ? (int64_t)deg_of(x[q]) : mx;
     }
     mx = block_max<int64_t>(mx, S->scr);
     co_after_heavy((int32_t)mx);
@@ -653,7 +666,6 @@ struct K {
       const int32_t r = a[q].x, v = a[q].y;
       const uint32_t d = deg_of(ldcg(B.st + v));
       set_rtag(B.rtag, v, (uint32_t)P().tag);
-      B.size[r] = 0;
       if (d == 0) {                             // no alive neighbour: singleton center
         B.st[v] = kLab + (uint32_t)r;
         t.centers += 1;
@@ -701,9 +713,12 @@ struct K {
       const int64_t wlo = P().win_lo, wlen = P().win_len;
       int64_t s, e;
       slice(wlo, wlen, &s, &e);
-      // the previous round's centers still hold the active marker: give them
-      // their labels (own rank) before this round marks new actives
-      if (P().r0 < 0) {
+      // C4: the previous round's centers still hold an active marker: give
+      // them their labels (own rank) before this round marks new actives.
+      // ClusterWild! centers keep kActive for good: no pass tells an old
+      // center from a current active by its word alone (they are filtered by
+      // the removal tag, and a center's label is its arank)
+      if (P().r0 < 0 && algo == kAlgoC4) {
         const int64_t pn = P().act_n;
         for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < pn; j += (int64_t)G * blockDim.x) {
           const int32_t v = ldcg(B.act_v + j);
@@ -1207,6 +1222,7 @@ __device__ bool team_permutation(K& k, uint64_t seed) {
     atomicAdd(&S.u.perm.hist[bits == 0 ? 0 : (int)(key >> (64 - bits))], 1);
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
     B.st[v] = kAlive | (uint32_t)d;
+    B.size[v] = 0;
   }
   for (int64_t i = tid; i < rtag_words(n); i += nthr) B.rtag[i] = 0;
   __syncthreads();
@@ -1391,6 +1407,7 @@ __global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
     B.st[v] = kAlive | (uint32_t)d;
+    B.size[v] = 0;                     // members per center rank
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rtag_words(n); i += (int64_t)gridDim.x * blockDim.x)
     B.rtag[i] = 0;
