@@ -247,6 +247,18 @@ int cc_server_wait(cc_server* s, int64_t ticket, int32_t* rounds, int64_t* disag
                    double* latency_ms);
 int cc_server_destroy(cc_server* s);
 
+/*
+ * Device memory.  Every device allocation of the library (graphs, clustering
+ * workspaces, batch and serving scratch) comes from one memory pool per GPU,
+ * owned by the library, on the caller's stream (stream-ordered).  Memory a
+ * destroyed graph or a finished batch gives back stays reserved in the pool,
+ * so the next graph of a similar size maps no new memory.  cc_release_memory
+ * returns the pools' unused reserved memory to the system (for example
+ * before handing the GPU to another allocator); memory still in use is not
+ * affected.  Returns CC_OK, or CC_ERR_CUDA.  The paper has no counterpart.
+ */
+int cc_release_memory(void);
+
 /* Human-readable name of a status code (static storage). */
 const char* cc_status_string(int status);
 

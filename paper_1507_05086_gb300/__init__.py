@@ -6,7 +6,7 @@ sm_103a CUDA kernels behind the C ABI of ``include/cc.h``.  This package is a
 thin ctypes binding over that library.
 """
 from .native import (ALGOS, C4, CLUSTERWILD, CCError, Graph, ROUND_STAT_FIELDS, Server, batch_jobs,
-                     batch_run, lib_path, load)
+                     batch_run, lib_path, load, release_memory)
 
 __all__ = ["ALGOS", "C4", "CLUSTERWILD", "CCError", "Graph", "ROUND_STAT_FIELDS", "Server", "batch_jobs",
-           "batch_run", "lib_path", "load"]
+           "batch_run", "lib_path", "load", "release_memory"]

@@ -15,6 +15,55 @@
 
 using namespace ccg;
 
+// ---- the library's device memory pools ---------------------------------------
+namespace {
+constexpr int kMaxPoolDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxPoolDevices] = {};
+}  // namespace
+
+namespace ccg {
+
+// One pool per device, created on first use, that keeps freed memory
+// reserved (release threshold: unlimited) so that repeated graph creation and
+// destruction does not map and unmap device memory every time.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxPoolDevices) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool;
+  {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps props = {};
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = dev;
+      cudaMemPool_t created;
+      if ((e = cudaMemPoolCreate(&created, &props)) != cudaSuccess) return e;
+      uint64_t keep = UINT64_MAX;
+      if ((e = cudaMemPoolSetAttribute(created, cudaMemPoolAttrReleaseThreshold, &keep)) != cudaSuccess) {
+        cudaMemPoolDestroy(created);
+        return e;
+      }
+      g_pool[dev] = created;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync(p, bytes, pool, stream);
+}
+
+}  // namespace ccg
+
+extern "C" int cc_release_memory(void) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  int rc = CC_OK;
+  for (int d = 0; d < kMaxPoolDevices; ++d)
+    if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], 0) != cudaSuccess) rc = CC_ERR_CUDA;
+  return rc;
+}
+
 namespace {
 // batched size classes: up to kBatchSmallN vertices one block runs a job, up
 // to kBatchTeamN a team of kBatchTeamBlocks blocks, beyond that the whole grid
@@ -50,7 +99,7 @@ bool is_device_ptr(const void* p) {
 template <class T>
 cudaError_t dalloc(T** p, size_t bytes, cudaStream_t s) {
   void* q = nullptr;
-  cudaError_t e = cudaMallocAsync(&q, bytes > 0 ? bytes : 1, s);
+  cudaError_t e = pool_malloc(&q, bytes > 0 ? bytes : 1, s);
   *p = static_cast<T*>(q);
   return e;
 }

@@ -11,6 +11,11 @@ namespace ccg {
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// ---- device memory (cc_api.cu) -----------------------------------------------
+// Stream-ordered allocation from the library's pool on the current device
+// (freed blocks stay reserved for reuse); free with cudaFreeAsync.
+cudaError_t pool_malloc(void** p, size_t bytes, cudaStream_t stream);
+
 // ---- permutation (cc_perm.cu) ----------------------------------------------
 int perm_bucket_bits(int64_t n);
 size_t perm_workspace_bytes(int64_t n);

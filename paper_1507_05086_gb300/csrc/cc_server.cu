@@ -106,7 +106,7 @@ int start_batch(cc_server* sv, Flight& f, std::vector<Request>& reqs) {
   const int teams = std::min<int>((int)reqs.size(), sv->grid);
   const size_t slot = align_up(batch_slot_bytes(n_max, 1));
   f.ws_bytes = slot * (size_t)teams;
-  cudaError_t e = cudaMallocAsync(&f.ws, f.ws_bytes, f.stream);
+  cudaError_t e = pool_malloc(&f.ws, f.ws_bytes, f.stream);
   if (e != cudaSuccess) return cuda_status(e);
   std::vector<RoundBuffers> slots((size_t)teams);
   for (int t = 0; t < teams; ++t) {
@@ -129,8 +129,8 @@ int start_batch(cc_server* sv, Flight& f, std::vector<Request>& reqs) {
     f.tickets.push_back(reqs[q].ticket);
     f.t_submit.push_back(reqs[q].t_submit);
   }
-  if ((e = cudaMallocAsync(&f.jobs_dev, sizeof(BatchJob) * f.jobs.size(), f.stream)) != cudaSuccess) return cuda_status(e);
-  if ((e = cudaMallocAsync(&f.slots_dev, sizeof(RoundBuffers) * slots.size(), f.stream)) != cudaSuccess)
+  if ((e = pool_malloc(reinterpret_cast<void**>(&f.jobs_dev), sizeof(BatchJob) * f.jobs.size(), f.stream)) != cudaSuccess) return cuda_status(e);
+  if ((e = pool_malloc(reinterpret_cast<void**>(&f.slots_dev), sizeof(RoundBuffers) * slots.size(), f.stream)) != cudaSuccess)
     return cuda_status(e);
   cudaMemcpyAsync(f.jobs_dev, f.jobs.data(), sizeof(BatchJob) * f.jobs.size(), cudaMemcpyHostToDevice, f.stream);
   cudaMemcpyAsync(f.slots_dev, slots.data(), sizeof(RoundBuffers) * slots.size(), cudaMemcpyHostToDevice, f.stream);

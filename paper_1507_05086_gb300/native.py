@@ -63,6 +63,8 @@ def load(build_if_missing: bool = True):
         vp, i64, i32, u32, u64, ci = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
                                        ctypes.c_uint64, ctypes.c_int)
         lib.cc_status_string.restype = ctypes.c_char_p
+        lib.cc_release_memory.restype = ci
+        lib.cc_release_memory.argtypes = []
         lib.cc_status_string.argtypes = [ci]
         lib.cc_graph_create.restype = ci
         lib.cc_graph_create.argtypes = [i64, vp, vp, u32, vp, ctypes.POINTER(vp)]
@@ -235,6 +237,11 @@ class Graph:
         d = ctypes.c_int64()
         _check("cc_disagreements", self._lib.cc_disagreements(self._h, _ptr(labels), ctypes.byref(d)))
         return d.value
+
+
+def release_memory():
+    """Return the unused device memory the library's pools keep reserved."""
+    _check("cc_release_memory", load().cc_release_memory())
 
 
 def batch_jobs(graphs, algo="cw", eps=0.5, seeds=None, k_perms=8):

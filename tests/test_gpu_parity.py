@@ -252,3 +252,45 @@ def test_batch_run_best_of_k(cc, ora, gg):
     finally:
         for x in graphs:
             x.close()
+
+
+def test_memory_pool_reuse_and_release(cc, ora, gg):
+    """Graphs created after a destroyed one reuse the pool; releasing the
+    unused reserve changes no result."""
+    g = gg.rmat(14, 8, seed=12)
+    order = ora.permutation(g.n, 5)
+    expect, er, _, _ = ora.rounds(g.off, g.col, order, 2, 0.5)
+    for round_ in range(3):
+        with cc.Graph(g.off, g.col) as graph:
+            lab, r, d = graph.cluster("cw", 0.5, 5)
+            assert np.array_equal(lab, expect) and r == er
+        if round_ == 1:
+            cc.release_memory()
+    cc.release_memory()
+
+
+def test_hubs_losing_degree_while_alive_match_oracle(cc, ora, gg):
+    """Three hubs of degree 66k-80k in a sparse background: their residual
+    degrees (and Delta) fall over several rounds before they are clustered."""
+    rng = np.random.default_rng(21)
+    n = 300_000
+    er = gg.erdos_renyi(n, 6.0 / n, seed=3)
+    src = [np.repeat(np.arange(n, dtype=np.int32), np.diff(er.off).astype(np.int64))]
+    dst = [er.col]
+    for h, deg in ((0, 80_000), (1, 70_000), (17, 66_000)):
+        leaves = rng.choice(n, deg + 10, replace=False).astype(np.int32)
+        leaves = leaves[leaves != h][:deg]
+        src.append(np.full(leaves.size, h, np.int32))
+        dst.append(leaves)
+    g = gg.from_edges(n, np.concatenate(src), np.concatenate(dst))
+    assert np.diff(g.off).max() >= 65535
+    with cc.Graph(g.off, g.col) as graph:
+        for algo, a in (("cw", 2), ("c4", 1)):
+            for eps, seed in ((0.5, 4), (0.9, 9)):
+                order = ora.permutation(g.n, seed)
+                olab, orr, _, ost = oracle_run(ora, g, order, a, eps)
+                lab, r, d, st = graph.cluster(algo, eps, seed, stats_cap=100_000)
+                assert np.array_equal(lab, olab) and r == orr, (algo, eps)
+                for f in STAT_FIELDS:
+                    assert np.array_equal(st[f], ost[f]), (algo, eps, f)
+                assert d == ora.disagreements(g.off, g.col, olab)
