@@ -72,6 +72,7 @@ constexpr int64_t kBatchTeamN = 1 << 21;
 constexpr int kBatchTeamBlocks = 8;
 }  // namespace
 
+
 namespace {
 
 int from_cuda(cudaError_t e) {
@@ -240,13 +241,33 @@ int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, 
         break;
       }
     }
-    // columns
+    // columns: from the host in kColChunks pieces on a copy stream, each
+    // checked on s as soon as it has landed, so validation hides under the
+    // transfer
+    const int chunks = (!dev && nnz > 0) ? kColChunks : 1;
+    int64_t cut[kColChunks + 1];
+    for (int c = 0; c <= chunks; ++c) cut[c] = nnz / chunks * c + (c == chunks ? nnz % chunks : 0);
     if (dev) {
       g->col = const_cast<int32_t*>(col_idx);
     } else {
       if ((rc = from_cuda(dalloc(&g->col, 4 * (size_t)nnz, s))) != CC_OK) break;
       g->own_col = true;
-      if (nnz > 0 && (rc = from_cuda(cudaMemcpyAsync(g->col, col_idx, 4 * (size_t)nnz, cudaMemcpyHostToDevice, s))) != CC_OK) break;
+      if (nnz > 0) {
+        cudaEvent_t alloc_done;
+        if ((rc = from_cuda(cudaStreamCreateWithFlags(&g->copy_stream, cudaStreamNonBlocking))) != CC_OK) break;
+        if ((rc = from_cuda(cudaEventCreateWithFlags(&alloc_done, cudaEventDisableTiming))) != CC_OK) break;
+        cudaEventRecord(alloc_done, s);                    // the allocation is ordered on s
+        cudaStreamWaitEvent(g->copy_stream, alloc_done, 0);
+        cudaEventDestroy(alloc_done);
+        for (int c = 0; c < chunks; ++c) {
+          if ((rc = from_cuda(cudaEventCreateWithFlags(&g->col_ready[c], cudaEventDisableTiming))) != CC_OK) break;
+          if ((rc = from_cuda(cudaMemcpyAsync(g->col + cut[c], col_idx + cut[c], 4 * (size_t)(cut[c + 1] - cut[c]),
+                                              cudaMemcpyHostToDevice, g->copy_stream))) != CC_OK)
+            break;
+          cudaEventRecord(g->col_ready[c], g->copy_stream);
+        }
+        if (rc != CC_OK) break;
+      }
     }
     // validation: offsets first (the non-empty-row list relies on them)
     void* vws = nullptr;
@@ -267,7 +288,11 @@ int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, 
     launch_nonempty_rows(n, g->off, g->nz_row, g->nz_pos, nws, nz_dev, g->num_sms, s);
     cudaMemcpyAsync(&g->nz_n, nz_dev, 8, cudaMemcpyDeviceToHost, s);
     if ((rc = from_cuda(cudaStreamSynchronize(s))) != CC_OK) { dfree(vws, s); dfree(nws, s); break; }
-    launch_validate_edges(n, nnz, g->nz_row, g->nz_pos, g->nz_n, g->col, vws, g->num_sms, s);
+    for (int c = 0; c < chunks; ++c) {
+      if (g->col_ready[c]) cudaStreamWaitEvent(s, g->col_ready[c], 0);
+      launch_validate_edges(n, cut[c], cut[c + 1], c == chunks - 1, g->nz_row, g->nz_pos, g->nz_n, g->col, vws,
+                            g->num_sms, s);
+    }
     cudaMemcpyAsync(vflags, vflags_dev, sizeof(vflags), cudaMemcpyDeviceToHost, s);
     dfree(vws, s);
     dfree(nws, s);
@@ -275,6 +300,15 @@ int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, 
     if ((rc = from_cuda(cudaGetLastError())) != CC_OK) break;
     if (vflags[0] != 0) { rc = CC_ERR_INVALID_GRAPH; break; }
   } while (false);
+  // the copy stream and its events are no longer needed (every chunk is
+  // ordered before the work on s, or the graph is being thrown away)
+  if (g->copy_stream) {
+    cudaStreamSynchronize(g->copy_stream);
+    for (auto& e : g->col_ready)
+      if (e) { cudaEventDestroy(e); e = nullptr; }
+    cudaStreamDestroy(g->copy_stream);
+    g->copy_stream = nullptr;
+  }
   if (rc != CC_OK) {
     cc_graph_destroy(g);
     return rc;

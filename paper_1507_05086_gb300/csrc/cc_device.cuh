@@ -317,27 +317,28 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
 }
 
 // gwarp / nwarps: this warp's index among, and the number of, the warps that
-// share the walk (the whole grid, or one team of blocks).  Warp w takes
-// chunks w, w + nwarps, ...
+// share the walk (the whole grid, or one team of blocks).  The walk covers
+// the virtual edges [E0, E); warp w takes chunks w, w + nwarps, ...
 template <class F>
 __device__ __forceinline__ void lbs_for_each_in(int64_t gwarp, int64_t nwarps, const int64_t* epos, int64_t nitems,
                                                 int64_t E, LbsWarp* ws, F&& f, const int64_t* delta = nullptr,
-                                                const int32_t* vtx = nullptr) {
-  if (E <= 0) return;
+                                                const int32_t* vtx = nullptr, int64_t E0 = 0) {
+  if (E <= E0) return;
   // up to kLbsBatches batches per chunk, fewer when the list is short, so
   // that short lists still spread over many warps
-  int64_t nb = E / (nwarps * (int64_t)kLbsW * 2);
+  int64_t nb = (E - E0) / (nwarps * (int64_t)kLbsW * 2);
   nb = nb < 1 ? 1 : (nb > kLbsBatches ? kLbsBatches : nb);
   const int64_t kChunk = (int64_t)kLbsW * nb;
-  for (int64_t c0 = gwarp * kChunk; c0 < E; c0 += nwarps * kChunk)
+  for (int64_t c0 = E0 + gwarp * kChunk; c0 < E; c0 += nwarps * kChunk)
     lbs_chunk(epos, nitems, c0, c0 + kChunk < E ? c0 + kChunk : E, ws, f, delta, vtx);
 }
 
 template <class F>
 __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems, int64_t E, LbsWarp* ws, F&& f,
-                                             const int64_t* delta = nullptr, const int32_t* vtx = nullptr) {
+                                             const int64_t* delta = nullptr, const int32_t* vtx = nullptr,
+                                             int64_t E0 = 0) {
   lbs_for_each_in(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5,
-                  epos, nitems, E, ws, f, delta, vtx);
+                  epos, nitems, E, ws, f, delta, vtx, E0);
 }
 
 // Lists of adjacency rows.  A list counter packs (items << 33 | edges): one

@@ -44,4 +44,8 @@ struct cc_graph {
   // pinned host staging for the small results
   ccg::Ctl* ctl_host = nullptr;
   unsigned long long* obj_host = nullptr;
+  // graph creation from host arrays: the column copy runs on its own stream
+  // in kColChunks pieces (released once creation ends)
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t col_ready[ccg::kColChunks] = {};
 };

@@ -11,6 +11,10 @@ namespace ccg {
 
 inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
 
+// pieces of the column array copied (and validated) one after another when a
+// graph is created from host memory
+constexpr int kColChunks = 8;
+
 // ---- device memory (cc_api.cu) -----------------------------------------------
 // Stream-ordered allocation from the library's pool on the current device
 // (freed blocks stay reserved for reuse); free with cudaFreeAsync.
@@ -162,8 +166,11 @@ size_t validate_workspace_bytes();
 // at ws + align_up(64) holds (first error code, max degree).
 cudaError_t launch_validate_offsets(int64_t n, int64_t nnz, const int64_t* off, void* ws, int num_sms,
                                     cudaStream_t stream);
-cudaError_t launch_validate_edges(int64_t n, int64_t nnz, const int32_t* nz_row, const int64_t* nz_pos,
-                                  int64_t nz_n, const int32_t* col, void* ws, int num_sms, cudaStream_t stream);
+// Entries [e0, e1) of the CSR; `last` adds the symmetry verdict over every
+// range validated since launch_validate_offsets cleared the workspace.
+cudaError_t launch_validate_edges(int64_t n, int64_t e0, int64_t e1, bool last, const int32_t* nz_row,
+                                  const int64_t* nz_pos, int64_t nz_n, const int32_t* col, void* ws, int num_sms,
+                                  cudaStream_t stream);
 cudaError_t launch_offsets_i32_to_i64(int64_t n, const int32_t* in, int64_t* out, cudaStream_t stream);
 size_t nonempty_workspace_bytes(int64_t n);
 cudaError_t launch_nonempty_rows(int64_t n, const int64_t* off, int32_t* nz_row, int64_t* nz_pos, void* ws,

@@ -88,7 +88,7 @@ __global__ void k_validate_offsets(int64_t n, int64_t nnz, const int64_t* __rest
 // lower and from the upper endpoint (equal multisets give equal sums).
 constexpr int kValThreads = 512;
 
-__global__ void __launch_bounds__(kValThreads) k_validate_edges(int64_t n, int64_t nnz, int64_t nz_n,
+__global__ void __launch_bounds__(kValThreads) k_validate_edges(int64_t n, int64_t e0, int64_t e1, int64_t nz_n,
                                                                const int32_t* __restrict__ nz_row,
                                                                const int64_t* __restrict__ nz_pos,
                                                                const int32_t* __restrict__ col, int* flags,
@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(kValThreads) k_validate_edges(int64_t n, int64
   unsigned long long lo1 = 0, lo2 = 0, up1 = 0, up2 = 0;
   long long nlo = 0, nup = 0;
   int bad = 0;
-  lbs_for_each(nz_pos, nz_n, nnz, &lbs[threadIdx.x >> 5], [&](const Lbs& L) {
+  lbs_for_each(nz_pos, nz_n, e1, &lbs[threadIdx.x >> 5], [&](const Lbs& L) {
 #pragma unroll
     for (int t = 0; t < kLbsK; ++t) {
       if (!L.ok(t)) continue;
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kValThreads) k_validate_edges(int64_t n, int64
       const uint64_t h1 = mix64(key ^ 0x9E3779B97F4A7C15ull), h2 = mix64(key + 0x632BE59BD9B4E019ull);
       if (u < w) { lo1 += h1; lo2 += h2; ++nlo; } else { up1 += h1; up2 += h2; ++nup; }
     }
-  });
+  }, nullptr, nullptr, e0);
   if (bad) atomicCAS(flags, 0, bad);
   lo1 = warp_sum(lo1); lo2 = warp_sum(lo2); up1 = warp_sum(up1); up2 = warp_sum(up2);
   nlo = warp_sum(nlo); nup = warp_sum(nup);
@@ -217,13 +217,14 @@ cudaError_t launch_validate_offsets(int64_t n, int64_t nnz, const int64_t* off, 
   return cudaGetLastError();
 }
 
-cudaError_t launch_validate_edges(int64_t n, int64_t nnz, const int32_t* nz_row, const int64_t* nz_pos,
-                                  int64_t nz_n, const int32_t* col, void* ws, int num_sms, cudaStream_t stream) {
+cudaError_t launch_validate_edges(int64_t n, int64_t e0, int64_t e1, bool last, const int32_t* nz_row,
+                                  const int64_t* nz_pos, int64_t nz_n, const int32_t* col, void* ws, int num_sms,
+                                  cudaStream_t stream) {
   unsigned long long* sums = static_cast<unsigned long long*>(ws);
   int* flags = reinterpret_cast<int*>(static_cast<char*>(ws) + align_up(8 * sizeof(unsigned long long)));
-  if (nnz > 0)
-    k_validate_edges<<<num_sms * 2, kValThreads, 0, stream>>>(n, nnz, nz_n, nz_row, nz_pos, col, flags, sums);
-  k_validate_symmetry<<<1, 1, 0, stream>>>(flags, sums);
+  if (e1 > e0)
+    k_validate_edges<<<num_sms * 2, kValThreads, 0, stream>>>(n, e0, e1, nz_n, nz_row, nz_pos, col, flags, sums);
+  if (last) k_validate_symmetry<<<1, 1, 0, stream>>>(flags, sums);
   return cudaGetLastError();
 }
 
