@@ -204,9 +204,12 @@ __device__ __forceinline__ int64_t warp_upper_bound(const int64_t* a, int64_t n,
 // needs none of the per-item loads: the warp keeps the range, delta and
 // vertex of its current item, taken from the previous batch's loads, and
 // only a batch that crosses an item boundary loads and scans item starts.
+// With vmap, the per-item payload is vmap[vtx[j]] - vsub instead of vtx[j]
+// (one load per item, not per edge).
 template <class F>
 __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, int64_t c0, int64_t cend, LbsWarp* ws,
-                                          F& f, const int64_t* delta, const int32_t* vtx) {
+                                          F& f, const int64_t* delta, const int32_t* vtx,
+                                          const uint32_t* vmap = nullptr, uint32_t vsub = 0) {
   const int lane = threadIdx.x & 31;
   int64_t j0 = warp_upper_bound(epos, nitems, c0) - 1;
   // cached item (warp-uniform): valid when cur_j == j0
@@ -249,6 +252,15 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
     }
     if (lane == 0) ws->next = -1;
     __syncwarp();
+    if (vmap) {
+      // payload of the items that own edges of this batch, and of the one
+      // that starts the next batch (it may be kept for that batch)
+#pragma unroll
+      for (int t = 0; t < kLbsK; ++t) {
+        const int i = lane + 32 * t;
+        if (s[t] <= base + kLbsW) ws->vtx[i] = (int32_t)(ldcg(vmap + ws->vtx[i]) - vsub);
+      }
+    }
 #pragma unroll
     for (int t = 0; t < kLbsK; ++t) {
       const int i = lane + 32 * t;
@@ -322,7 +334,8 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
 template <class F>
 __device__ __forceinline__ void lbs_for_each_in(int64_t gwarp, int64_t nwarps, const int64_t* epos, int64_t nitems,
                                                 int64_t E, LbsWarp* ws, F&& f, const int64_t* delta = nullptr,
-                                                const int32_t* vtx = nullptr, int64_t E0 = 0) {
+                                                const int32_t* vtx = nullptr, int64_t E0 = 0,
+                                                const uint32_t* vmap = nullptr, uint32_t vsub = 0) {
   if (E <= E0) return;
   // up to kLbsBatches batches per chunk, fewer when the list is short, so
   // that short lists still spread over many warps
@@ -330,7 +343,7 @@ __device__ __forceinline__ void lbs_for_each_in(int64_t gwarp, int64_t nwarps, c
   nb = nb < 1 ? 1 : (nb > kLbsBatches ? kLbsBatches : nb);
   const int64_t kChunk = (int64_t)kLbsW * nb;
   for (int64_t c0 = E0 + gwarp * kChunk; c0 < E; c0 += nwarps * kChunk)
-    lbs_chunk(epos, nitems, c0, c0 + kChunk < E ? c0 + kChunk : E, ws, f, delta, vtx);
+    lbs_chunk(epos, nitems, c0, c0 + kChunk < E ? c0 + kChunk : E, ws, f, delta, vtx, vmap, vsub);
 }
 
 template <class F>

@@ -145,9 +145,10 @@ struct K {
 
   template <class F>
   __device__ __forceinline__ void lbs(const int64_t* epos, int64_t nitems, int64_t E, F&& f,
-                                      const int64_t* delta = nullptr, const int32_t* vtx = nullptr) {
+                                      const int64_t* delta = nullptr, const int32_t* vtx = nullptr,
+                                      const uint32_t* vmap = nullptr, uint32_t vsub = 0) {
     lbs_for_each_in(((int64_t)bid * blockDim.x + threadIdx.x) >> 5, ((int64_t)G * blockDim.x) >> 5, epos, nitems,
-                    E, lbs_ws(), f, delta, vtx);
+                    E, lbs_ws(), f, delta, vtx, 0, vmap, vsub);
   }
 
   __device__ __forceinline__ const Plan& P() const { return S->plan; }
@@ -1048,7 +1049,7 @@ struct K {
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         w[q] = L.ok(q) ? __ldg(B.col + L.csr(q)) : 0;
-        lu[q] = L.ok(q) ? ldcg(B.st + L.vtx(q)) - kLab : 0;     // the member's (final) label
+        lu[q] = (uint32_t)L.vtx(q);                             // the member's (final) label
       }
       uint32_t tg[kLbsK];
 #pragma unroll
@@ -1072,7 +1073,7 @@ struct K {
           t.mm += 1;
         }
       }
-    }, B.new_d, B.new_v);
+    }, B.new_d, B.new_v, B.st, kLab);       // payload: the member's label, st[v] - kLab
   }
 
   // Reduce the round tallies of this block into the control block.
