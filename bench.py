@@ -148,13 +148,13 @@ def measured_hbm_peak():
 
 # DRAM traffic of the round kernel per algorithmic byte, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on R-MAT scale 24,
-# ClusterWild!, eps 0.5: 5.973 GB against 4.497 GB algorithmic), keyed by a
+# ClusterWild!, eps 0.5: 6.197 GB against 4.497 GB algorithmic), keyed by a
 # digest of the kernel's sources: a changed kernel reports traffic null until
 # it is captured again.  Traffic grows with the scanned entries and vertices,
 # so the ratio scales the capture to the timed workload.
 ROUNDS_SOURCES = ("paper_1507_05086_gb300/csrc/cc_rounds.cu", "paper_1507_05086_gb300/csrc/cc_device.cuh",
                   "paper_1507_05086_gb300/csrc/cc_internal.h")
-ROUNDS_TRAFFIC_PER_BYTE = {"0d2e6549c119bf47": 5.973120e9 / 4.497261200e9}
+ROUNDS_TRAFFIC_PER_BYTE = {"15b763dcd22b4057": 6.196875e9 / 4.497261200e9}
 
 
 def rounds_sources_digest() -> str:
@@ -164,6 +164,30 @@ def rounds_sources_digest() -> str:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def measure_gather_ceiling(torch, device, table_words: int = 1 << 23, reads: int = 1 << 28) -> float:
+    """Random 4-byte reads per second of a library gather (torch.index_select
+    with int32 indices) from a table of `table_words` words (32 MiB: the size
+    of the round kernel's removal-tag array at 2^26 vertices, held in L2),
+    indices streamed from memory: the access pattern of the round kernel's
+    adjacency passes, one random neighbour read per streamed column id."""
+    g = torch.Generator(device=device)
+    g.manual_seed(7)
+    table = torch.randint(0, 1 << 30, (table_words,), dtype=torch.int32, device=device, generator=g)
+    idx = torch.randint(0, table_words, (reads,), dtype=torch.int32, device=device, generator=g)
+    out = torch.empty(reads, dtype=torch.int32, device=device)
+    for _ in range(3):
+        torch.index_select(table, 0, idx, out=out)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    s.record()
+    for _ in range(reps):
+        torch.index_select(table, 0, idx, out=out)
+    e.record()
+    torch.cuda.synchronize()
+    return reads * reps / (s.elapsed_time(e) / 1e3)
 
 
 def rounds_algorithmic_bytes(edges_scanned: int, n: int) -> int:
@@ -370,6 +394,13 @@ def run_ours(args):
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_rounds", "peak_kind": peak_kind,
                 "bytes_per_launch": sum(rk_bytes) / len(rk_bytes), "ms_per_launch": sum(rk_ms) / len(rk_ms)}
+    # the same kernel against the random-read rate a library gather reaches
+    # on this GPU: every scanned adjacency entry costs one random 4-byte read
+    ceiling = measure_gather_ceiling(torch, torch.device("cuda", local_rank))
+    rk_edges = sum(e for a in algos for e in per[a]["edges"])
+    random_access = {"achieved": rk_edges / (sum(rk_ms) / 1e3), "ceiling": ceiling, "unit": "random reads/s",
+                     "frac": rk_edges / (sum(rk_ms) / 1e3) / ceiling, "kernel": "k_rounds",
+                     "ceiling_kind": "measured: torch.index_select, int32 indices, 2^28 reads from a 32 MiB table"}
 
     # end to end through the public API with host buffers
     e2e = None
@@ -433,6 +464,7 @@ def run_ours(args):
             "e2e": e2e,
             "gpu_launches": KERNELS_PER_CLUSTERING * clusterings,
             "roofline": roofline,
+            "random_access": random_access,
             "cpu_baseline": cpu,
             "batch": batch,
             "serve": serve,
