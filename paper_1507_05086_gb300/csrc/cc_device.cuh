@@ -149,8 +149,19 @@ __device__ __forceinline__ T block_max(T x, T* scratch) {
 // lanes still take part in warp collectives).
 // ---------------------------------------------------------------------------
 constexpr int kLbsK = 4;
+#ifndef CC_LBS_PF_AHEAD
+#define CC_LBS_PF_AHEAD 2
+#endif
+constexpr int kLbsPfAhead = CC_LBS_PF_AHEAD;   // batches of a long row prefetched into L2 ahead
+
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
 constexpr int kLbsW = 32 * kLbsK;
-constexpr int kLbsBatches = 8;
+#ifndef CC_LBS_BATCHES
+#define CC_LBS_BATCHES 8
+#endif
+constexpr int kLbsBatches = CC_LBS_BATCHES;   // batches per chunk of a long walk
 
 struct LbsWarp {
   int32_t mark[kLbsW];   // relative item index per position
@@ -206,10 +217,16 @@ __device__ __forceinline__ int64_t warp_upper_bound(const int64_t* a, int64_t n,
 // only a batch that crosses an item boundary loads and scans item starts.
 // With vmap, the per-item payload is vmap[vtx[j]] - vsub instead of vtx[j]
 // (one load per item, not per edge).
+//
+// With colp (the CSR column array; the walk's CSR position of virtual edge e
+// of item j is e + delta[j], or e without delta), the column ids of the
+// batch kLbsPfAhead ahead in the current row are prefetched into L2, so a
+// long row streams from DRAM ahead of its use.  E: the walk's end.
 template <class F>
 __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, int64_t c0, int64_t cend, LbsWarp* ws,
                                           F& f, const int64_t* delta, const int32_t* vtx,
-                                          const uint32_t* vmap = nullptr, uint32_t vsub = 0) {
+                                          const uint32_t* vmap = nullptr, uint32_t vsub = 0,
+                                          const int32_t* colp = nullptr, int64_t E = 0) {
   const int lane = threadIdx.x & 31;
   int64_t j0 = warp_upper_bound(epos, nitems, c0) - 1;
   // cached item (warp-uniform): valid when cur_j == j0
@@ -233,6 +250,10 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
       for (int t = 0; t < kLbsK; ++t) {
         L.ri[t] = 0;
         if (base + lane + 32 * t < cend) L.valid |= 1u << t;
+      }
+      if (colp && lane < kLbsW / 32) {
+        const int64_t pe = base + (int64_t)kLbsPfAhead * kLbsW + 32 * lane;
+        if (pe < cur_end && pe < E) prefetch_l2(colp + pe + cur_dlt);
       }
       f(L);
       __syncwarp();
@@ -321,6 +342,13 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
       cur_end = r1 == INT32_MAX ? INT64_MAX : base + r1;
       cur_dlt = delta ? ws->dlt[m] : 0;
       cur_vtx = vtx ? ws->vtx[m] : 0;
+      // the next batches of that item: start streaming them
+      if (colp) {
+        for (int a = 1; a <= kLbsPfAhead; ++a) {
+          const int64_t pe = base + (int64_t)a * kLbsW + 32 * lane;
+          if (lane < kLbsW / 32 && pe >= cur_start && pe < cur_end && pe < E) prefetch_l2(colp + pe + cur_dlt);
+        }
+      }
     }
     f(L);
     __syncwarp();
@@ -335,7 +363,8 @@ template <class F>
 __device__ __forceinline__ void lbs_for_each_in(int64_t gwarp, int64_t nwarps, const int64_t* epos, int64_t nitems,
                                                 int64_t E, LbsWarp* ws, F&& f, const int64_t* delta = nullptr,
                                                 const int32_t* vtx = nullptr, int64_t E0 = 0,
-                                                const uint32_t* vmap = nullptr, uint32_t vsub = 0) {
+                                                const uint32_t* vmap = nullptr, uint32_t vsub = 0,
+                                                const int32_t* colp = nullptr) {
   if (E <= E0) return;
   // up to kLbsBatches batches per chunk, fewer when the list is short, so
   // that short lists still spread over many warps
@@ -343,15 +372,15 @@ __device__ __forceinline__ void lbs_for_each_in(int64_t gwarp, int64_t nwarps, c
   nb = nb < 1 ? 1 : (nb > kLbsBatches ? kLbsBatches : nb);
   const int64_t kChunk = (int64_t)kLbsW * nb;
   for (int64_t c0 = E0 + gwarp * kChunk; c0 < E; c0 += nwarps * kChunk)
-    lbs_chunk(epos, nitems, c0, c0 + kChunk < E ? c0 + kChunk : E, ws, f, delta, vtx, vmap, vsub);
+    lbs_chunk(epos, nitems, c0, c0 + kChunk < E ? c0 + kChunk : E, ws, f, delta, vtx, vmap, vsub, colp, E);
 }
 
 template <class F>
 __device__ __forceinline__ void lbs_for_each(const int64_t* epos, int64_t nitems, int64_t E, LbsWarp* ws, F&& f,
                                              const int64_t* delta = nullptr, const int32_t* vtx = nullptr,
-                                             int64_t E0 = 0) {
+                                             int64_t E0 = 0, const int32_t* colp = nullptr) {
   lbs_for_each_in(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5, ((int64_t)gridDim.x * blockDim.x) >> 5,
-                  epos, nitems, E, ws, f, delta, vtx, E0);
+                  epos, nitems, E, ws, f, delta, vtx, E0, nullptr, 0, colp);
 }
 
 // Lists of adjacency rows.  A list counter packs (items << 33 | edges): one

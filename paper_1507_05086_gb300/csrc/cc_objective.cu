@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kObjThreads) k_intra(int64_t nz_n, const int32
 #pragma unroll
     for (int t = 0; t < kLbsK; ++t)
       if (L.ok(t)) cnt += (__ldg(labels + w[t]) == lu[t]) ? 1 : 0;
-  });
+  }, nullptr, nullptr, 0, col);
   cnt = block_sum<int64_t>(cnt, scr);
   if (threadIdx.x == 0 && cnt) atomicAdd(out + 0, (unsigned long long)cnt);
 }
@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kValThreads) k_validate_edges(int64_t n, int64
       const uint64_t h1 = mix64(key ^ 0x9E3779B97F4A7C15ull), h2 = mix64(key + 0x632BE59BD9B4E019ull);
       if (u < w) { lo1 += h1; lo2 += h2; ++nlo; } else { up1 += h1; up2 += h2; ++nup; }
     }
-  }, nullptr, nullptr, e0);
+  }, nullptr, nullptr, e0, col);
   if (bad) atomicCAS(flags, 0, bad);
   lo1 = warp_sum(lo1); lo2 = warp_sum(lo2); up1 = warp_sum(up1); up2 = warp_sum(up2);
   nlo = warp_sum(nlo); nup = warp_sum(nup);

@@ -86,6 +86,7 @@ __device__ __forceinline__ void atom_add_release(unsigned* p, unsigned v) {
 struct Coord {
   int64_t n, n_alive, cursor, al_len, k, round, stats_cap, eps_ppm;
   int64_t need, win_lo, win_len, r_edges, fix_iter;
+  int64_t clusters;              // centers opened so far
   int64_t h_len, nz_len, nz_total;
   int32_t tau, delta, max_deg, d_new;
   int algo, al_sel, al_ident, rebuilds_in_row;
@@ -127,9 +128,12 @@ struct Shared {
 };
 
 // Per-thread tallies of one round (flushed at every round end).
+// The member-center edges of the objective need no tally: every member of a
+// cluster is adjacent to its center (it was attached through that edge) and
+// to no other center of its cluster, so they number n - (number of clusters).
 struct Tally {
   int32_t centers, attached, noncenter, blocked;
-  uint32_t mc, mm;              // member-center and member-member edges
+  uint32_t mm;                  // member-member entries inside a cluster
 };
 
 // The blocks that run one clustering job: the whole grid, or a team of
@@ -147,8 +151,9 @@ struct K {
   __device__ __forceinline__ void lbs(const int64_t* epos, int64_t nitems, int64_t E, F&& f,
                                       const int64_t* delta = nullptr, const int32_t* vtx = nullptr,
                                       const uint32_t* vmap = nullptr, uint32_t vsub = 0) {
+    // every walk with a delta array walks CSR rows: stream them ahead
     lbs_for_each_in(((int64_t)bid * blockDim.x + threadIdx.x) >> 5, ((int64_t)G * blockDim.x) >> 5, epos, nitems,
-                    E, lbs_ws(), f, delta, vtx, 0, vmap, vsub);
+                    E, lbs_ws(), f, delta, vtx, 0, vmap, vsub, delta ? B.col : nullptr);
   }
 
   __device__ __forceinline__ const Plan& P() const { return S->plan; }
@@ -293,6 +298,7 @@ struct K {
       c.nz_static = 1;
       c.nz_sel = 0;
       c.round = 0;
+      c.clusters = 0;
       c.rebuilds_in_row = 0;
       c.algo = vload(&C->algo);
       c.eps_ppm = vload(&C->eps_ppm);
@@ -437,6 +443,7 @@ struct K {
       c.round_t0 = globaltimer_ns();
       if (centers_seen != centers) fail(kErrInternal);
       c.n_alive -= removed;
+      c.clusters += centers;
       if (c.n_alive < 0) fail(kErrInternal);
       c.round = r + 1;
       c.rebuilds_in_row = 0;
@@ -849,10 +856,7 @@ struct K {
     // degree 1: nothing to decrement, and no other center can reach it, so
     // its label is already final.
     const bool single = fresh && d_old == 1;
-    if (single) {
-      t.mc += 1;
-      atomicAdd(B.size + r, 1);          // one more member (result unused)
-    }
+    if (single) atomicAdd(B.size + r, 1);   // one more member (result unused)
     const bool want = fresh && d_old != 1;
     int64_t row = 0;
     int32_t len = 0;
@@ -1067,8 +1071,7 @@ struct K {
           atomicSub(B.st + w[q], 1u);                          // result unused
         } else if (tg[q] != tag) {
           continue;
-        } else if (is_active(x[q])) {                          // a center of this round
-          if ((uint32_t)ldcg(B.arank + w[q]) == lu[q]) t.mc += 1;
+        } else if (is_active(x[q])) {                          // a center of this round: counted per member
         } else if (x[q] - kLab == lu[q]) {
           t.mm += 1;
         }
@@ -1078,15 +1081,15 @@ struct K {
 
   // Reduce the round tallies of this block into the control block.
   __device__ void flush_round_tallies() {
-    const long long v[6] = {t.centers, t.attached, t.noncenter, t.blocked, (long long)t.mc, (long long)t.mm};
-    long long* dst[6] = {&C->r_centers, &C->r_attached, &C->r_noncenter, &C->r_blocked,
-                         reinterpret_cast<long long*>(&C->mc), reinterpret_cast<long long*>(&C->mm)};
+    const long long v[5] = {t.centers, t.attached, t.noncenter, t.blocked, (long long)t.mm};
+    long long* dst[5] = {&C->r_centers, &C->r_attached, &C->r_noncenter, &C->r_blocked,
+                         reinterpret_cast<long long*>(&C->mm)};
 #pragma unroll
-    for (int i = 0; i < 6; ++i) {
+    for (int i = 0; i < 5; ++i) {
       const long long s = block_sum<int64_t>(v[i], S->scr);
       if (threadIdx.x == 0 && s != 0) atomicAdd(reinterpret_cast<unsigned long long*>(dst[i]), (unsigned long long)s);
     }
-    t = Tally{0, 0, 0, 0, 0, 0};
+    t = Tally{0, 0, 0, 0, 0};
   }
 };
 
@@ -1178,6 +1181,7 @@ out:
   if (k.bid == 0 && threadIdx.x == 0) {
     C->round = S.co.round;
     C->n_alive = S.co.n_alive;
+    C->mc = (unsigned long long)(S.co.n - S.co.clusters);   // member-center edges
     C->done = S.plan.state == kDone ? 1 : 0;
     for (int i = 0; i < 8; ++i) C->ph_ns[i] = S.co.ph_ns[i];
   }
@@ -1186,7 +1190,7 @@ out:
 __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ RoundBuffers B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Shared& S = *reinterpret_cast<Shared*>(smem_raw);
-  K k{B, B.ctl, &S, gridDim.x, blockIdx.x, 0u, Tally{0, 0, 0, 0, 0, 0}};
+  K k{B, B.ctl, &S, gridDim.x, blockIdx.x, 0u, Tally{0, 0, 0, 0, 0}};
   if ((threadIdx.x & 31) == 0) S.u.w.app[threadIdx.x >> 5].n = 0;
   __syncthreads();
   run_job(k, vload(&B.ctl->algo));
@@ -1332,7 +1336,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
   const unsigned team = blockIdx.x / G, nteams = gridDim.x / G;
   if (team >= nteams) return;
   Ctl* C = slots[team].ctl;
-  K k{rb, C, &S, G, blockIdx.x % G, 0u, Tally{0, 0, 0, 0, 0, 0}};
+  K k{rb, C, &S, G, blockIdx.x % G, 0u, Tally{0, 0, 0, 0, 0}};
   if (threadIdx.x == 0) S.plan.state = kDone;
   __syncthreads();
   for (int j = (int)team; j < njobs; j += (int)nteams) {
