@@ -54,6 +54,7 @@ constexpr int kScanU = 4;                    // alive-list entries per thread pe
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
 constexpr int kRun = 0, kDone = 1, kRebuild = 2, kAbort = 3, kRebuildDelta = 4, kScanH = 5;
 constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
+constexpr int64_t kInlineDecide = 4096;      // C4 blocked lists up to this size are decided by the coordinator
 
 // State word of a vertex (uint32):
 //   alive ........... kAlive | residual degree
@@ -247,7 +248,8 @@ struct K {
   }
 
   __device__ RowList new_list() const { return RowList{B.new_v, B.new_e, B.new_d, nullptr, &C->new_pack}; }
-  __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, nullptr, &C->blk_pack}; }
+  // blocked actives; the payload initialises each one's pull slot (no center yet)
+  __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, B.pull, &C->blk_pack}; }
   __device__ LbsWarp* lbs_ws() const { return &S->u.w.lbs[threadIdx.x >> 5]; }
   __device__ AppendBuf* app_buf() const { return &S->u.w.app[threadIdx.x >> 5]; }
 
@@ -933,17 +935,7 @@ struct K {
           t.centers += 1;
         }
       }
-      warp_append_rows(blocked, (int32_t)j, row, len, 0, blk_list());
-    }
-  }
-
-  // Reset the per-item scratch of the blocked list (after its counter is known).
-  __device__ void c4_blocked_init() {
-    const int64_t bn = P().b_n;
-    for (int64_t q = bid * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
-      B.hit_c[q] = 0;
-      B.hit_p[q] = 0;
-      B.pull[q] = 0x7FFFFFFF;
+      warp_append_rows(blocked, (int32_t)j, row, len, 0x7FFFFFFF, blk_list());
     }
   }
 
@@ -969,11 +961,13 @@ struct K {
     });
   }
 
-  // C4 fixpoint, step 2: decide (isCenter without waiting).
-  __device__ long long c4_fix_decide() {
+  // C4 fixpoint, step 2: decide (isCenter without waiting) for blocked items
+  // q = first, first + stride, ...  The hit flags go back to zero, so they
+  // are zero whenever a fixpoint starts.
+  __device__ long long c4_fix_decide(int64_t first, int64_t stride) {
     const int64_t bn = P().b_n;
     long long left = 0;
-    for (int64_t q = bid * (int64_t)blockDim.x + threadIdx.x; q < bn; q += (int64_t)G * blockDim.x) {
+    for (int64_t q = first; q < bn; q += stride) {
       const int32_t j = ldcg(B.b_j + q);
       const int32_t v = ldcg(B.act_v + j), r = ldcg(B.act_r + j);
       (void)r;
@@ -1143,27 +1137,32 @@ __device__ void run_job(K& k, int algo) {
             }))
           goto out;
         if (S.plan.b_n > 0) {
-          k.c4_blocked_init();
-          if (!k.sync(5, [&] {
-                if (threadIdx.x == 0) C->undecided = 0;
-              }))
-            goto out;
+          // the pull slots were set when the list was built; the hit flags are zero
+          auto after_decide = [&](long long left) {
+            if (threadIdx.x == 0) {
+              S.plan.undecided = left;
+              S.co.fix_iter += 1;
+              if (S.co.fix_iter > 1) S.co.r_edges += S.plan.b_E;
+              if (S.co.fix_iter > S.plan.b_n + 1) { k.fail(kErrInternal); S.plan.undecided = 0; }
+            }
+          };
           while (S.plan.undecided > 0) {
             k.c4_fix_scan();
-            if (!k.sync(5)) goto out;
-            const long long left = block_sum<int64_t>(k.c4_fix_decide(), S.scr);
-            if (threadIdx.x == 0 && left)
-              atomicAdd(reinterpret_cast<unsigned long long*>(&C->undecided), (unsigned long long)left);
-            if (!k.sync(5, [&] {
-                  if (threadIdx.x == 0) {
-                    S.plan.undecided = vload(&C->undecided);
-                    C->undecided = 0;
-                    S.co.fix_iter += 1;
-                    if (S.co.fix_iter > 1) S.co.r_edges += S.plan.b_E;
-                    if (S.co.fix_iter > S.plan.b_n + 1) { k.fail(kErrInternal); S.plan.undecided = 0; }
-                  }
-                }))
-              goto out;
+            if (S.plan.b_n <= kInlineDecide) {
+              // a short blocked list: the coordinator decides inside the barrier
+              if (!k.sync(5, [&] {
+                    const long long left = block_sum<int64_t>(k.c4_fix_decide(threadIdx.x, blockDim.x), S.scr);
+                    after_decide(left);
+                  }))
+                goto out;
+            } else {
+              if (!k.sync(5, [&] { if (threadIdx.x == 0) C->undecided = 0; })) goto out;
+              const long long left = block_sum<int64_t>(
+                  k.c4_fix_decide((int64_t)k.bid * blockDim.x + threadIdx.x, (int64_t)k.G * blockDim.x), S.scr);
+              if (threadIdx.x == 0 && left)
+                atomicAdd(reinterpret_cast<unsigned long long*>(&C->undecided), (unsigned long long)left);
+              if (!k.sync(5, [&] { after_decide((long long)vload(&C->undecided)); })) goto out;
+            }
           }
           k.c4_blocked_attach();
           if (!k.sync(5)) goto out;
@@ -1228,6 +1227,8 @@ __device__ bool team_permutation(K& k, uint64_t seed) {
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
     B.st[v] = kAlive | (uint32_t)d;
     B.size[v] = 0;
+    B.hit_c[v] = 0;
+    B.hit_p[v] = 0;
   }
   for (int64_t i = tid; i < rtag_words(n); i += nthr) B.rtag[i] = 0;
   __syncthreads();
@@ -1413,6 +1414,8 @@ __global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm) {
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
     B.st[v] = kAlive | (uint32_t)d;
     B.size[v] = 0;                     // members per center rank
+    B.hit_c[v] = 0;                    // C4 fixpoint flags start (and stay) zero
+    B.hit_p[v] = 0;
   }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rtag_words(n); i += (int64_t)gridDim.x * blockDim.x)
     B.rtag[i] = 0;
