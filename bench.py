@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "edges/s clustered (C4 + ClusterWild!, eps=0.5) at 1B edges"
 SAMPLE_SCALE = 22          # CPU sample: same R-MAT generator, 1/16 of the vertices
-KERNELS_PER_CLUSTERING = 8  # 5 permutation kernels + state init + rounds + labels
+KERNELS_PER_CLUSTERING = 10  # 7 permutation kernels + state init + rounds + labels
 
 
 def parse_args(argv=None):

@@ -34,30 +34,51 @@ __global__ void k_bucket_hist(int64_t n, uint64_t seed, int bits, uint32_t* __re
     atomicAdd(&count[bucket_of(perm_key(seed, (uint64_t)v), bits)], 1u);
 }
 
-// Exclusive scan of nb counts by one block; start[nb] = n.  cursor = start.
-__global__ void k_bucket_scan(const uint32_t* __restrict__ count, int64_t nb, int64_t* __restrict__ start,
-                              int64_t* __restrict__ cursor) {
+// Exclusive scan of the nb counts into start[0..nb] (start[nb] = n) and
+// cursor = start, in three steps: every block of kScanTile threads scans its
+// tile of counts (tile totals to tot[]), one block scans the totals, every
+// block adds its tile's offset.
+constexpr int kScanTile = 1024;
+
+__global__ void __launch_bounds__(kScanTile) k_scan_tiles(const uint32_t* __restrict__ count, int64_t nb,
+                                                        int64_t* __restrict__ start, int64_t* __restrict__ tot) {
   __shared__ int64_t scratch[33];
-  const int64_t per = (nb + blockDim.x - 1) / blockDim.x;
-  const int64_t lo = threadIdx.x * per, hi = lo + per < nb ? lo + per : nb;
-  int64_t s = 0;
-  for (int64_t i = lo; i < hi; ++i) s += count[i];
-  int64_t total;
-  int64_t run = block_exclusive_sum<int64_t>(s, scratch, &total);
-  for (int64_t i = lo; i < hi; ++i) {
-    start[i] = run;
-    cursor[i] = run;
-    run += count[i];
-  }
-  if (threadIdx.x == 0) start[nb] = total;
+  const int64_t i = blockIdx.x * (int64_t)kScanTile + threadIdx.x;
+  int64_t t;
+  const int64_t ex = block_exclusive_sum<int64_t>(i < nb ? (int64_t)count[i] : 0, scratch, &t);
+  if (i < nb) start[i] = ex;
+  if (threadIdx.x == 0) tot[blockIdx.x] = t;
 }
 
-__global__ void k_bucket_scatter(int64_t n, uint64_t seed, int bits, int64_t* __restrict__ cursor,
+__global__ void k_scan_totals(int64_t ntiles, int64_t nb, int64_t* __restrict__ tot, int64_t* __restrict__ start) {
+  __shared__ int64_t scratch[33];
+  int64_t run = 0;
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    const int64_t i = base + threadIdx.x;
+    int64_t t;
+    const int64_t ex = block_exclusive_sum<int64_t>(i < ntiles ? tot[i] : 0, scratch, &t);
+    if (i < ntiles) tot[i] = run + ex;
+    run += t;
+  }
+  if (threadIdx.x == 0) start[nb] = run;
+}
+
+__global__ void __launch_bounds__(kScanTile) k_scan_add(int64_t nb, const int64_t* __restrict__ tot,
+                                                      int64_t* __restrict__ start, uint32_t* __restrict__ cursor) {
+  const int64_t i = blockIdx.x * (int64_t)kScanTile + threadIdx.x;
+  if (i < nb) {
+    const int64_t s = start[i] + tot[blockIdx.x];
+    start[i] = s;
+    cursor[i] = (uint32_t)s;              // positions are below n < 2^31
+  }
+}
+
+__global__ void k_bucket_scatter(int64_t n, uint64_t seed, int bits, uint32_t* __restrict__ cursor,
                                  int32_t* __restrict__ tmp) {
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
        v += (int64_t)gridDim.x * blockDim.x) {
     uint32_t b = bucket_of(perm_key(seed, (uint64_t)v), bits);
-    int64_t pos = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&cursor[b]), 1ull);
+    const int64_t pos = (int64_t)atomicAdd(&cursor[b], 1u);
     tmp[pos] = (int32_t)v;
   }
 }
@@ -185,7 +206,7 @@ size_t perm_workspace_bytes(int64_t n) {
   const int64_t nb = int64_t(1) << perm_bucket_bits(n);
   return align_up(sizeof(uint32_t) * nb) + align_up(sizeof(int64_t) * (nb + 1)) +
          align_up(sizeof(int64_t) * nb) + align_up(sizeof(int32_t) * (n > 0 ? n : 1)) +
-         align_up(sizeof(int) * (kMaxOverflow + 1));
+         align_up(sizeof(int) * (kMaxOverflow + 1)) + align_up(sizeof(int64_t) * ((nb + kScanTile - 1) / kScanTile));
 }
 
 // order[0..n) = pi for `seed`.  ws must hold perm_workspace_bytes(n).  A
@@ -198,9 +219,11 @@ cudaError_t launch_permutation(int64_t n, uint64_t seed, int32_t* order, void* w
   char* p = static_cast<char*>(ws);
   uint32_t* count = reinterpret_cast<uint32_t*>(p); p += align_up(sizeof(uint32_t) * nb);
   int64_t* start = reinterpret_cast<int64_t*>(p);   p += align_up(sizeof(int64_t) * (nb + 1));
-  int64_t* cursor = reinterpret_cast<int64_t*>(p);  p += align_up(sizeof(int64_t) * nb);
+  uint32_t* cursor = reinterpret_cast<uint32_t*>(p); p += align_up(sizeof(int64_t) * nb);
   int32_t* tmp = reinterpret_cast<int32_t*>(p);     p += align_up(sizeof(int32_t) * n);
-  int* overflow = reinterpret_cast<int*>(p);
+  int* overflow = reinterpret_cast<int*>(p);         p += align_up(sizeof(int) * (kMaxOverflow + 1));
+  int64_t* tot = reinterpret_cast<int64_t*>(p);
+  const int64_t stiles = (nb + kScanTile - 1) / kScanTile;
   cudaError_t e = cudaMemsetAsync(count, 0, sizeof(uint32_t) * nb, stream);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(overflow, 0, sizeof(int), stream);
@@ -208,7 +231,9 @@ cudaError_t launch_permutation(int64_t n, uint64_t seed, int32_t* order, void* w
   const int64_t want = (n + 255) / 256;
   const int grid = (int)(want < (int64_t)num_sms * 8 ? want : (int64_t)num_sms * 8);
   k_bucket_hist<<<grid, 256, 0, stream>>>(n, seed, bits, count);
-  k_bucket_scan<<<1, 1024, 0, stream>>>(count, nb, start, cursor);
+  k_scan_tiles<<<(unsigned)stiles, kScanTile, 0, stream>>>(count, nb, start, tot);
+  k_scan_totals<<<1, 1024, 0, stream>>>(stiles, nb, tot, start);
+  k_scan_add<<<(unsigned)stiles, kScanTile, 0, stream>>>(nb, tot, start, cursor);
   k_bucket_scatter<<<grid, 256, 0, stream>>>(n, seed, bits, cursor, tmp);
   const int sgrid = (int)(nb < (int64_t)num_sms * 4 ? nb : (int64_t)num_sms * 4);
   k_bucket_sort<<<sgrid, kSortThreads, 0, stream>>>(seed, bits, nb, start, tmp, order, overflow);

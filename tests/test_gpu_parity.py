@@ -66,6 +66,32 @@ def test_permutation_matches_oracle(cc, ora, gg, n, seed):
         assert np.array_equal(graph.permutation(seed), ora.permutation(n, seed))
 
 
+def _splitmix64_np(x):
+    """The published SplitMix64 output for state x (numpy, uint64 wrap-around)."""
+    with np.errstate(over="ignore"):
+        z = x + np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+@pytest.mark.parametrize("n,seed", [(1 << 26, 9), (110_000_003, 4)])
+def test_permutation_large_is_sorted_by_key(cc, gg, n, seed):
+    """At the bench size (shared-memory bucket counters) and above 10^8
+    vertices (global counters): pi is a permutation and ascending in
+    (splitmix64(seed ^ v), v), which defines it uniquely."""
+    off = np.zeros(n + 1, np.int64)
+    with cc.Graph(off, np.zeros(0, np.int32)) as graph:
+        order = graph.permutation(seed)
+    assert order.shape == (n,)
+    seen = np.zeros(n, np.bool_)
+    seen[order] = True
+    assert seen.all()
+    keys = _splitmix64_np(np.uint64(seed) ^ order.astype(np.uint64))
+    ka, kb = keys[:-1], keys[1:]
+    assert bool(np.all((ka < kb) | ((ka == kb) & (order[:-1] < order[1:]))))
+
+
 @pytest.mark.parametrize("algo", ["c4", "cw"])
 @pytest.mark.parametrize("eps", [0.1, 0.5, 0.9, 1.0])
 def test_cluster_matches_oracle(cc, ora, gg, algo, eps):
