@@ -1,0 +1,32 @@
+"""The quality study (quality.py) on the 10k Erdos-Renyi workload: its data
+come from the batched entry point and the per-round statistics, so they are
+checked against the oracle job by job (C4 objective = KwikCluster's, the
+blocked share = the oracle's blocked counts, ClusterWild! = the oracle's
+rounds)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_quality_study_matches_oracle(cc, ora, gg):
+    import quality
+    g = gg.erdos_renyi(10_000, 20.0 / 9_999.0, seed=0)
+    perms, stats_perms, seed = 6, 3, 300
+    r = quality.study(cc, g, 0.5, perms, stats_perms, seed)
+    d_kc, d_cw, rounds_cw, blocked = [], [], [], []
+    for j in range(perms):
+        order = ora.permutation(g.n, seed + j)
+        d_kc.append(ora.disagreements(g.off, g.col, ora.kwik(g.off, g.col, order)))
+        lab, rr, _, st = ora.rounds(g.off, g.col, order, ora.ALGO_CW, 0.5, stats_cap=10_000)
+        d_cw.append(ora.disagreements(g.off, g.col, lab))
+        rounds_cw.append(rr)
+        if j < stats_perms:
+            _, _, _, st4 = ora.rounds(g.off, g.col, order, ora.ALGO_C4, 0.5, stats_cap=10_000)
+            blocked.append(st4["blocked"].sum() / g.n * 100)
+    assert r["objective_c4_equals_kwikcluster"]["mean"] == pytest.approx(np.mean(d_kc), rel=0, abs=1e-9)
+    assert r["objective_c4_equals_kwikcluster"]["max"] == max(d_kc)
+    assert r["objective_cw"]["mean"] == pytest.approx(np.mean(d_cw), rel=0, abs=1e-9)
+    assert r["rounds_cw"]["max"] == max(rounds_cw)
+    assert r["c4_blocked_pct_of_vertices"]["mean"] == pytest.approx(np.mean(blocked), rel=1e-12)
+    assert r["cw_over_c4"]["mean"] == pytest.approx(np.mean(np.array(d_cw) / np.array(d_kc)), rel=1e-12)
