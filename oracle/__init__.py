@@ -69,6 +69,17 @@ def _load():
         lib.orc_rounds.restype = ctypes.c_int
         lib.orc_rounds.argtypes = [i64, i64p, i32p, i32p, ctypes.c_int, i64, ctypes.c_int,
                                    i32p, i64p, i32p, ctypes.c_void_p, i64]
+        lib.orc_rounds_bsp.restype = ctypes.c_int
+        lib.orc_rounds_bsp.argtypes = [i64, i64p, i32p, i32p, ctypes.c_int, i64, u64,
+                                       i32p, i64p, i32p, ctypes.c_void_p, i64]
+        lib.orc_bsp_period.restype = i64
+        lib.orc_bsp_period.argtypes = [i64, i64, i64]
+        lib.orc_bsp_delta_hat.restype = i64
+        lib.orc_bsp_delta_hat.argtypes = [i64, i64, i64]
+        lib.orc_bsp_threshold.restype = u64
+        lib.orc_bsp_threshold.argtypes = [i64, i64, ctypes.POINTER(ctypes.c_int)]
+        lib.orc_bsp_batch.restype = i64
+        lib.orc_bsp_batch.argtypes = [u64, i64, i64, u64, ctypes.c_int]
         lib.orc_disagreements_pairs.restype = i64
         lib.orc_disagreements_pairs.argtypes = [i64, i64p, i32p, i32p]
         lib.orc_disagreements.restype = i64
@@ -158,6 +169,56 @@ def rounds(off, col, order, algo: int, eps: float, delta_mode: int = 1,
                  for f in ROUND_STAT_FIELDS}
     return lab[:n], r, (ar[:n] if ar is not None else None), stats
 
+
+
+def bsp_period(n: int, max_deg: int, eps: float) -> int:
+    """Rounds between two halvings of Delta-hat (Sec. 5, reading R13)."""
+    return int(_load().orc_bsp_period(n, max_deg, eps_to_ppm(eps)))
+
+
+def bsp_delta_hat(max_deg: int, period: int, round_: int) -> int:
+    return int(_load().orc_bsp_delta_hat(max_deg, period, round_))
+
+
+def bsp_threshold(eps: float, delta_hat: int):
+    """(T, all): a trial succeeds when its draw is below T, or always (R14)."""
+    a = ctypes.c_int(0)
+    t = int(_load().orc_bsp_threshold(eps_to_ppm(eps), delta_hat, ctypes.byref(a)))
+    return t, bool(a.value)
+
+
+def bsp_batch(seed: int, round_: int, trials: int, thr: int, all_: bool) -> int:
+    """B_i: successes among `trials` Bernoulli trials of round `round_` (R14)."""
+    return int(_load().orc_bsp_batch(ctypes.c_uint64(seed & (2**64 - 1)), round_, trials,
+                                      ctypes.c_uint64(thr), 1 if all_ else 0))
+
+
+def rounds_bsp(off, col, order, algo: int, eps: float, seed: int, stats_cap: int = 0,
+               want_active_round: bool = False):
+    """C4 / ClusterWild! rounds with the practical schedule of Sec. 5 (Delta-hat
+    halving, binomial batches over the unprocessed suffix of pi; seed = the
+    seed of pi).  Returns (labels, rounds, active_round or None, stats or None)."""
+    off, col = _csr(off, col)
+    n = off.size - 1
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    lab = np.empty(max(n, 1), np.int32)
+    nr = np.zeros(1, np.int64)
+    ar = np.empty(max(n, 1), np.int32) if want_active_round else None
+    st = (_RoundStat * stats_cap)() if stats_cap > 0 else None
+    rc = _load().orc_rounds_bsp(n, _p(off), _p(col), _p(order), algo, eps_to_ppm(eps),
+                                ctypes.c_uint64(seed & (2**64 - 1)), _p(lab), _p(nr),
+                                _p(ar) if ar is not None else ctypes.c_void_p(0),
+                                ctypes.cast(st, ctypes.c_void_p) if st is not None else ctypes.c_void_p(0),
+                                stats_cap)
+    if rc != 0:
+        raise RuntimeError(f"orc_rounds_bsp failed: {rc}")
+    r = int(nr[0])
+    stats = None
+    if st is not None:
+        cnt = min(r, stats_cap)
+        stats = {f: np.array([getattr(st[i], f) for i in range(cnt)], np.int64)
+                 for f in ROUND_STAT_FIELDS}
+    return lab[:n], r, (ar[:n] if ar is not None else None), stats
 
 def disagreements_pairs(off, col, labels) -> int:
     """O(n^2) recount over all unordered pairs (Sec. 2 definition)."""

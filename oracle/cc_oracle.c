@@ -41,6 +41,25 @@
  *      ClusterWild!'s createCluster skips the active set (Gamma(v) \ A).
  *   R8 clusterID holds the center's rank; the reported label is the center's
  *      vertex id.
+ *
+ * The practical schedule of Sec. 5 ("Estimating but not computing Delta",
+ * "Binomial sampling instead of fixed-size batches"), orc_rounds_bsp:
+ *   R13 the proxy Delta-hat starts at the maximum degree and halves every P
+ *      rounds, P = ceil((2/eps) ln(n log Delta / delta)) with delta = 1/10,
+ *      computed in integers: ln x = ln 2 * log2 x with log2 x rounded up to a
+ *      bit length, P = ceil(2 * 693147 * L / eps_ppm), L = bits(n) +
+ *      bits(bits(max(Delta, 2))) + 4 (bits(x) = number of binary digits, and
+ *      4 = bits(10) for 1/delta).  Delta-hat_i = max(1, Delta >> floor(i / P)).
+ *   R14 B_i ~ Bin(N_i, eps / Delta-hat_i) with N_i the unprocessed suffix of
+ *      pi (ranks cursor .. n-1, clustered or not), drawn as the number of
+ *      successes of N_i Bernoulli trials: trial j succeeds when the j-th
+ *      output of SplitMix64 seeded with s_i = splitmix64(seed ^ C ^ i)
+ *      (C = 0x5851F42D4C957F2D) is below T_i = floor(eps_ppm 2^64 /
+ *      (10^6 Delta-hat_i)); every trial succeeds when eps_ppm = 10^6 and
+ *      Delta-hat_i = 1.
+ *   R15 A_i = the alive vertices among the next B_i ranks of pi; the cursor
+ *      moves past all B_i.  Rounds continue while a vertex is unclustered (a
+ *      round may have no active vertex).
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -130,6 +149,67 @@ typedef struct {
     int64_t blocked;   /* C4: actives with an earlier alive neighbour       */
 } orc_round_stat;
 
+/* ---- Sec. 5 schedule (readings R13-R15) ----------------------------------- */
+static int64_t orc_bits(uint64_t x)
+{
+    int64_t b = 0;
+    while (x) { ++b; x >>= 1; }
+    return b;
+}
+
+/* Rounds between two halvings of Delta-hat (R13). */
+int64_t orc_bsp_period(int64_t n, int64_t max_deg, int64_t eps_ppm)
+{
+    const int64_t d = max_deg > 2 ? max_deg : 2;
+    const int64_t l = orc_bits((uint64_t)n) + orc_bits((uint64_t)orc_bits((uint64_t)d)) + 4;
+    const uint64_t num = 2ull * 693147ull * (uint64_t)l;
+    return (int64_t)((num + (uint64_t)eps_ppm - 1) / (uint64_t)eps_ppm);
+}
+
+/* Delta-hat of round i (R13). */
+int64_t orc_bsp_delta_hat(int64_t max_deg, int64_t period, int64_t round)
+{
+    const int64_t h = round / period;
+    const int64_t d = h >= 63 ? 0 : (max_deg >> h);
+    return d > 1 ? d : 1;
+}
+
+/* T = floor(eps_ppm 2^64 / (10^6 dhat)) by long division, 12 bits at a time
+ * (the remainder stays below 2^51); *all = 1 when every trial succeeds. */
+uint64_t orc_bsp_threshold(int64_t eps_ppm, int64_t dhat, int *all)
+{
+    const uint64_t den = 1000000ull * (uint64_t)dhat;
+    *all = (uint64_t)eps_ppm >= den;
+    if (*all) return UINT64_MAX;
+    uint64_t r = (uint64_t)eps_ppm, t = 0;
+    for (int step = 0; step < 5; ++step) {            /* 60 bits */
+        r <<= 12;
+        t = (t << 12) | (r / den);
+        r %= den;
+    }
+    r <<= 4;                                          /* the last 4 bits */
+    t = (t << 4) | (r / den);
+    return t;
+}
+
+/* B_i: successes among the N trials of round i (R14). */
+int64_t orc_bsp_batch(uint64_t seed, int64_t round, int64_t trials, uint64_t thr, int all)
+{
+    if (all) return trials;
+    const uint64_t s = orc_splitmix64(seed ^ 0x5851F42D4C957F2Dull ^ (uint64_t)round);
+    int64_t b = 0;
+    uint64_t state = s;
+    for (int64_t j = 0; j < trials; ++j) {
+        state += 0x9E3779B97F4A7C15ull;          /* the SplitMix64 generator: */
+        uint64_t z = state;                      /* advance, then mix          */
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        b += z < thr;
+    }
+    return b;
+}
+
 /* Round-i batch size (readings R3, R4). */
 int64_t orc_batch_size(int64_t eps_ppm, int64_t n_i, int64_t delta_i)
 {
@@ -152,10 +232,10 @@ int64_t orc_batch_size(int64_t eps_ppm, int64_t n_i, int64_t delta_i)
  * which v was in the active set, or -1.  stats (optional) receives up to
  * stats_cap rounds.  Returns the number of rounds through *rounds_out.
  */
-int orc_rounds(int64_t n, const int64_t *off, const int32_t *col,
-               const int32_t *order, int algo, int64_t eps_ppm, int delta_mode,
-               int32_t *label_out, int64_t *rounds_out, int32_t *active_round,
-               orc_round_stat *stats, int64_t stats_cap)
+static int rounds_impl(int64_t n, const int64_t *off, const int32_t *col,
+                       const int32_t *order, int algo, int64_t eps_ppm, int delta_mode,
+                       uint64_t seed, int32_t *label_out, int64_t *rounds_out,
+                       int32_t *active_round, orc_round_stat *stats, int64_t stats_cap)
 {
     if (n < 0 || eps_ppm < 1 || eps_ppm > 1000000) return ORC_ERR_ARG;
     if (algo != ORC_ALGO_C4 && algo != ORC_ALGO_CW) return ORC_ERR_ARG;
@@ -186,23 +266,39 @@ int orc_rounds(int64_t n, const int64_t *off, const int32_t *col,
         if (active_round) active_round[v] = -1;
     }
     int64_t n_alive = n, cursor = 0, rounds = 0, top = maxdeg0;
+    const int64_t period = delta_mode == 2 ? orc_bsp_period(n, maxdeg0, eps_ppm) : 0;
     int status = ORC_OK;
 
     while (n_alive > 0) {                                    /* while V != empty */
-        /* Delta = max residual degree over alive vertices (R5) */
-        int64_t delta = 0;
-        if (delta_mode == 0) {
-            for (int64_t v = 0; v < n; ++v)
-                if (alive[v] && deg[v] > delta) delta = deg[v];
+        int64_t delta = 0, na = 0;
+        if (delta_mode == 2) {
+            /* Sec. 5: Delta-hat, B ~ Bin(unprocessed, eps / Delta-hat), A = the
+             * alive vertices among the next B of pi (R13-R15) */
+            if (cursor >= n) { status = ORC_ERR_STATE; goto done; }
+            delta = orc_bsp_delta_hat(maxdeg0, period, rounds);
+            int all;
+            const uint64_t thr = orc_bsp_threshold(eps_ppm, delta, &all);
+            const int64_t b = orc_bsp_batch(seed, rounds, n - cursor, thr, all);
+            for (int64_t r = cursor; r < cursor + b; ++r) {
+                int32_t v = order[r];
+                if (alive[v]) { act[na++] = v; in_a[v] = 1; }
+            }
+            cursor += b;
         } else {
-            while (top > 0 && cnt[top] == 0) --top;
-            delta = top;
-        }
-        /* A = the first k alive vertices of pi (R3, R4) */
-        int64_t k = orc_batch_size(eps_ppm, n_alive, delta), na = 0;
-        while (na < k) {
-            int32_t v = order[cursor++];
-            if (alive[v]) { act[na++] = v; in_a[v] = 1; }
+            /* Delta = max residual degree over alive vertices (R5) */
+            if (delta_mode == 0) {
+                for (int64_t v = 0; v < n; ++v)
+                    if (alive[v] && deg[v] > delta) delta = deg[v];
+            } else {
+                while (top > 0 && cnt[top] == 0) --top;
+                delta = top;
+            }
+            /* A = the first k alive vertices of pi (R3, R4) */
+            int64_t k = orc_batch_size(eps_ppm, n_alive, delta);
+            while (na < k) {
+                int32_t v = order[cursor++];
+                if (alive[v]) { act[na++] = v; in_a[v] = 1; }
+            }
         }
         int64_t centers = 0, blocked = 0, nr = 0;
         /* process A in pi order: attemptCluster (C4) or createCluster (CW) */
@@ -273,6 +369,28 @@ done:
     free(rank); free(cid); free(deg); free(alive); free(in_a); free(center);
     free(act); free(rem); free(cnt);
     return status;
+}
+
+int orc_rounds(int64_t n, const int64_t *off, const int32_t *col,
+               const int32_t *order, int algo, int64_t eps_ppm, int delta_mode,
+               int32_t *label_out, int64_t *rounds_out, int32_t *active_round,
+               orc_round_stat *stats, int64_t stats_cap)
+{
+    if (delta_mode != 0 && delta_mode != 1) return ORC_ERR_ARG;
+    return rounds_impl(n, off, col, order, algo, eps_ppm, delta_mode, 0, label_out, rounds_out,
+                       active_round, stats, stats_cap);
+}
+
+/* The practical schedule of Sec. 5 (R13-R15): same rounds, Delta-hat and the
+ * binomial batch of seed `seed` (the seed of pi).  stats[i].delta holds
+ * Delta-hat_i and stats[i].k the number of active vertices. */
+int orc_rounds_bsp(int64_t n, const int64_t *off, const int32_t *col,
+                   const int32_t *order, int algo, int64_t eps_ppm, uint64_t seed,
+                   int32_t *label_out, int64_t *rounds_out, int32_t *active_round,
+                   orc_round_stat *stats, int64_t stats_cap)
+{
+    return rounds_impl(n, off, col, order, algo, eps_ppm, 2, seed, label_out, rounds_out,
+                       active_round, stats, stats_cap);
 }
 
 /* ------------------------------------------------------------------------ */

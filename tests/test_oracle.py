@@ -279,3 +279,128 @@ def test_planted_labels_of_noise_free_partition_cost_zero(ora, gg):
     assert ora.disagreements(g.off, g.col, g.aux) == 0
     order = ora.permutation(g.n, 1)
     assert ora.disagreements(g.off, g.col, ora.kwik(g.off, g.col, order)) == 0
+
+
+# ---- the practical schedule of Sec. 5 (Delta-hat halving, binomial batches) ----
+_GAMMA = 0x9E3779B97F4A7C15
+_M64 = (1 << 64) - 1
+
+
+def _py_splitmix64_np(x):
+    """SplitMix64 output function on a uint64 array (x already advanced)."""
+    with np.errstate(over="ignore"):
+        z = x.astype(np.uint64)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def _py_period(n, max_deg, eps_ppm):
+    bits = lambda x: int(x).bit_length()
+    L = bits(n) + bits(bits(max(max_deg, 2))) + 4
+    return -(-2 * 693147 * L // eps_ppm)
+
+
+def _py_delta_hat(max_deg, period, i):
+    h = i // period
+    return max(1, (max_deg >> h) if h < 63 else 0)
+
+
+def _py_threshold(eps_ppm, dh):
+    den = 10**6 * dh
+    return None if eps_ppm >= den else (eps_ppm << 64) // den
+
+
+def _py_batch(seed, i, trials, thr):
+    if thr is None:
+        return trials
+    s = ((seed ^ 0x5851F42D4C957F2D ^ i) + _GAMMA) & _M64
+    z = s
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _M64
+    s = z ^ (z >> 31)
+    j = np.arange(1, trials + 1, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        states = np.uint64(s) + j * np.uint64(_GAMMA)
+    return int((_py_splitmix64_np(states) < np.uint64(thr)).sum())
+
+
+def test_bsp_schedule_matches_closed_forms(ora):
+    """Period, Delta-hat, threshold and batch draw of the Sec. 5 schedule
+    re-derived in Python integers and numpy (readings R13, R14)."""
+    for n, D, eps in ((10_000, 40, 0.5), (1, 0, 1.0), (67_108_864, 1_003_939, 0.5), (5, 3, 0.1), (999, 1, 0.9)):
+        ppm = ora.eps_to_ppm(eps)
+        P = ora.bsp_period(n, D, eps)
+        assert P == _py_period(n, D, ppm)
+        for i in (0, 1, P - 1, P, 3 * P + 2, 80 * P):
+            assert ora.bsp_delta_hat(D, P, i) == _py_delta_hat(D, P, i)
+    assert ora.bsp_period(67_108_864, 1_003_939, 0.5) == 100
+    for ppm, dh in ((500_000, 40), (1_000_000, 1), (1, 2**31 - 1), (999_999, 1), (100_000, 3), (1_000_000, 2)):
+        t, all_ = ora.bsp_threshold(ppm / 1e6, dh)
+        want = _py_threshold(ppm, dh)
+        assert all_ == (want is None)
+        if want is not None:
+            assert t == want
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        seed, i, trials = int(rng.integers(0, 2**63)), int(rng.integers(0, 500)), int(rng.integers(0, 20_000))
+        thr = int(rng.integers(0, 2**63)) * 2
+        assert ora.bsp_batch(seed, i, trials, thr, False) == _py_batch(seed, i, trials, thr)
+    # the draw is a binomial: its mean over many rounds is trials * p
+    thr = _py_threshold(500_000, 40)
+    draws = [ora.bsp_batch(7, i, 10_000, thr, False) for i in range(400)]
+    assert abs(np.mean(draws) - 10_000 / 80) < 4 * np.sqrt(10_000 / 80 / 400)
+
+
+def _check_bsp_windows(off, col, order, labels, ar, stats, eps, seed):
+    """A_i = the alive vertices among ranks [c_i, c_i + B_i) with B_i the
+    round's binomial draw over n - c_i trials (R15), Delta-hat_i in the stats."""
+    n = off.size - 1
+    D = int(np.diff(off).max()) if n else 0
+    ppm = round(eps * 10**6)
+    P = _py_period(n, D, ppm)
+    rr = chk.removal_rounds(labels, ar)
+    R = len(stats["k"])
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+    c = 0
+    for i in range(R):
+        dh = _py_delta_hat(D, P, i)
+        b = _py_batch(seed, i, n - c, _py_threshold(ppm, dh))
+        window = order[c:c + b]
+        alive_in_window = window[rr[window] >= i]
+        assert np.array_equal(np.sort(np.nonzero(ar == i)[0]), np.sort(alive_in_window)), i
+        assert stats["delta"][i] == dh and stats["k"][i] == alive_in_window.size
+        assert stats["n_alive"][i] == int((rr >= i).sum())
+        c += b
+    assert int((rr >= R).sum()) == 0
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.5, 1.0])
+def test_bsp_c4_equals_kwikcluster(ora, gg, eps):
+    """Serializability holds for any batch sequence: C4 with the Sec. 5
+    schedule is KwikCluster under pi."""
+    for gi, g in enumerate(_graphs(gg, 21)):
+        for seed in (0, 3, 2**50 + 1):
+            order = ora.permutation(g.n, seed)
+            lab, r, ar, st = ora.rounds_bsp(g.off, g.col, order, ora.ALGO_C4, eps, seed,
+                                            stats_cap=100000, want_active_round=True)
+            assert np.array_equal(lab, ora.kwik(g.off, g.col, order)), (gi, seed)
+            if g.n:
+                _check_bsp_windows(g.off, g.col, order, lab, ar, st, eps, seed)
+
+
+@pytest.mark.parametrize("eps", [0.1, 0.9])
+def test_bsp_clusterwild_equals_kwikcluster_on_noisy_graph(ora, gg, eps):
+    """ClusterWild! with the Sec. 5 schedule is KwikCluster on G-hat (edges
+    inside one round's active set deleted)."""
+    for gi, g in enumerate(_graphs(gg, 22)):
+        for seed in (1, 6):
+            order = ora.permutation(g.n, seed)
+            lab, r, ar, st = ora.rounds_bsp(g.off, g.col, order, ora.ALGO_CW, eps, seed,
+                                            stats_cap=100000, want_active_round=True)
+            off2, col2 = chk.noisy_graph(g.off, g.col, ar)
+            assert np.array_equal(lab, ora.kwik(off2, col2, order)), (gi, seed)
+            chk.check_partition_invariants(g.off, g.col, lab)
+            if g.n:
+                _check_bsp_windows(g.off, g.col, order, lab, ar, st, eps, seed)
