@@ -63,6 +63,20 @@ extern "C" {
 /* ---- algorithms ---------------------------------------------------------- */
 #define CC_ALGO_C4          1     /* serializable: equals KwikCluster(pi)          */
 #define CC_ALGO_CLUSTERWILD 2     /* coordination-free                             */
+/* The same two with the practical schedule of Sec. 5 (estimating Delta,
+ * binomial batches) instead of Alg. 2's exact Delta_i and k_i:
+ *   Delta-hat starts at the maximum degree and halves every
+ *   P = ceil(2 * 693147 * L / eps_ppm) rounds, L = bits(n) +
+ *   bits(bits(max(Delta, 2))) + 4 (the paper's (2/eps) ln(n log Delta /
+ *   delta) with delta = 1/10, logarithms rounded up to bit lengths);
+ *   B_i = the number of the round's n - cursor draws below
+ *   floor(eps_ppm 2^64 / (10^6 Delta-hat_i)) (all when that is 2^64), draw j
+ *   being the j-th output of SplitMix64 seeded with
+ *   splitmix64(seed ^ 0x5851F42D4C957F2D ^ i), seed = the seed of pi;
+ *   A_i = the alive vertices among the next B_i ranks of pi.
+ * cc_round_stats.delta then reports Delta-hat_i and .k the active count. */
+#define CC_ALGO_C4_EST          3
+#define CC_ALGO_CLUSTERWILD_EST 4
 
 /* ---- cc_graph_create flags ----------------------------------------------- */
 #define CC_DEVICE_PTRS  2u   /* row_offsets/col_idx are device pointers, adopted by
@@ -119,7 +133,8 @@ int cc_permutation(cc_graph* g, uint64_t seed, int32_t* order_out);
 
 /*
  * cc_cluster -- one full clustering (Alg. 2) of graph g.
- *   algo               CC_ALGO_C4 or CC_ALGO_CLUSTERWILD.
+ *   algo               CC_ALGO_C4, CC_ALGO_CLUSTERWILD, CC_ALGO_C4_EST or
+ *                      CC_ALGO_CLUSTERWILD_EST.
  *   eps                0 < eps <= 1 (Sec. 3 assumes eps <= 1).
  *   seed               selects pi.
  *   labels_out         int32[n], host or device memory: the center vertex id

@@ -346,7 +346,7 @@ int cc_permutation(cc_graph* g, uint64_t seed, int32_t* order_out) {
 int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
                   int64_t* disagreements_out, cc_round_stats* stats, int32_t stats_cap, int32_t* stats_len) {
   if (!g) return CC_ERR_INVALID_ARG;
-  if (algo != CC_ALGO_C4 && algo != CC_ALGO_CLUSTERWILD) return CC_ERR_INVALID_ARG;
+  if (algo < CC_ALGO_C4 || algo > CC_ALGO_CLUSTERWILD_EST) return CC_ERR_INVALID_ARG;
   if (stats_cap < 0 || (stats_cap > 0 && !stats)) return CC_ERR_INVALID_ARG;
   int64_t ppm = 0;
   int rc = eps_ppm_of(eps, &ppm);
@@ -381,7 +381,7 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[0], s));
   CC_TRY(launch_permutation(g->n, seed, g->order, g->perm_ws, g->num_sms, g->perm_err, s));
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[1], s));
-  CC_TRY(launch_rounds(b, algo, ppm, g->grid, s));
+  CC_TRY(launch_rounds(b, algo, ppm, seed, g->grid, s));
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[2], s));
   const bool dev = is_device_ptr(labels_out);
   if (labels_out && !dev) {
@@ -482,7 +482,7 @@ namespace {
 int run_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, const uint64_t* seeds, int32_t k_perms,
                    std::vector<BatchJob>& jobs) {
   if (count < 0 || k_perms < 1 || (count > 0 && (!gs || !seeds))) return CC_ERR_INVALID_ARG;
-  if (algo != CC_ALGO_C4 && algo != CC_ALGO_CLUSTERWILD) return CC_ERR_INVALID_ARG;
+  if (algo < CC_ALGO_C4 || algo > CC_ALGO_CLUSTERWILD_EST) return CC_ERR_INVALID_ARG;
   int64_t ppm = 0;
   int rc = eps_ppm_of(eps, &ppm);
   if (rc != CC_OK) return rc;

@@ -49,8 +49,9 @@ static_assert(offsetof(Plan, state) == 112, "the state word opens the last 16 by
 struct Ctl {
   unsigned arrive, gen;           // grid barrier (monotonic counters)
   int err;
-  int algo;
+  int algo;                       // 1 / 2: C4 / ClusterWild!; 3 / 4: the same with the Sec. 5 schedule
   int64_t eps_ppm;
+  uint64_t seed;                  // seed of pi (the Sec. 5 batch draws derive from it)
   alignas(16) Plan plan;
   // per-round counters, written by every block (lists pack items << 33 | edges)
   unsigned long long act_pack, new_pack, blk_pack;
@@ -147,7 +148,8 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid);
 void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* b);
 // Largest co-resident grid for the persistent round kernel on this device.
 int rounds_grid_size(int device);
-cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, int grid, cudaStream_t stream);
+cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, uint64_t seed, int grid,
+                          cudaStream_t stream);
 // labels_out[v] = center vertex id (order[center rank]) when labels_out is
 // not null; always adds the pair term sum_c C(s_c, 2) to ctl->pairs.
 cudaError_t launch_finalize_labels(const RoundBuffers& b, int32_t* labels_out, cudaStream_t stream);

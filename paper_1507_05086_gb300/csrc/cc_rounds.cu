@@ -52,7 +52,7 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanU = 4;                    // alive-list entries per thread per scan step
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
-constexpr int kRun = 0, kDone = 1, kRebuild = 2, kAbort = 3, kRebuildDelta = 4, kScanH = 5;
+constexpr int kRun = 0, kDone = 1, kRebuild = 2, kAbort = 3, kRebuildDelta = 4, kScanH = 5, kDrawBatch = 6;
 constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
 constexpr int64_t kInlineDecide = 4096;      // C4 blocked lists up to this size are decided by the coordinator
 
@@ -76,6 +76,49 @@ __device__ __forceinline__ void set_rtag(uint32_t* rtag, int32_t v, uint32_t tag
   atomicOr(rtag + (v >> 3), tag << ((v & 7) * 4));      // result unused
 }
 
+// ---- the practical schedule of Sec. 5 ------------------------------------------
+// Delta-hat starts at the maximum degree and halves every P rounds,
+// P = (2/eps) ln(n log Delta / delta) with delta = 1/10, in integers: ln x =
+// ln 2 log2 x with log2 rounded up to a bit length.  The batch B_i is
+// binomial over the n - cursor unprocessed ranks of pi with p = eps /
+// Delta-hat_i: the number of the round's SplitMix64 draws (a stream seeded
+// from the seed of pi and the round) below T_i = floor(p 2^64).  A_i = the
+// alive vertices among the next B_i ranks.
+__device__ __forceinline__ int64_t bit_length(uint64_t x) { return x ? 64 - __clzll((long long)x) : 0; }
+
+__device__ __forceinline__ int64_t sec5_period(int64_t n, int64_t max_deg, int64_t eps_ppm) {
+  const int64_t l = bit_length((uint64_t)n) + bit_length((uint64_t)bit_length((uint64_t)(max_deg > 2 ? max_deg : 2))) + 4;
+  return (int64_t)((2ull * 693147ull * (uint64_t)l + (uint64_t)eps_ppm - 1) / (uint64_t)eps_ppm);
+}
+
+__device__ __forceinline__ int64_t sec5_delta_hat(int64_t max_deg, int64_t period, int64_t round) {
+  const int64_t h = round / period;
+  const int64_t d = h >= 63 ? 0 : (max_deg >> h);
+  return d > 1 ? d : 1;
+}
+
+// floor(eps_ppm 2^64 / (10^6 dhat)) for eps_ppm < 10^6 dhat: 64 quotient bits
+// by long division (12, 12, 12, 12, 12, 4 bits; the remainder stays < 2^51).
+__device__ __forceinline__ uint64_t sec5_threshold(int64_t eps_ppm, int64_t dhat, bool* all) {
+  const uint64_t den = 1000000ull * (uint64_t)dhat;
+  *all = (uint64_t)eps_ppm >= den;
+  if (*all) return ~0ull;
+  uint64_t r = (uint64_t)eps_ppm, t = 0;
+#pragma unroll
+  for (int s = 0; s < 5; ++s) {
+    r <<= 12;
+    t = (t << 12) | (r / den);
+    r %= den;
+  }
+  r <<= 4;
+  return (t << 4) | (r / den);
+}
+
+// Draw j of round i's stream: the j-th output of SplitMix64 seeded with s.
+__device__ __forceinline__ uint64_t sec5_draw(uint64_t s, uint64_t j) {
+  return perm_key(0, s + j * 0x9E3779B97F4A7C15ull);     // state s + (j+1) gamma, mixed
+}
+
 template <class T>
 __device__ __forceinline__ T vload(const T* p) { return *reinterpret_cast<const volatile T*>(p); }
 
@@ -92,6 +135,9 @@ struct Coord {
   int32_t tau, delta, max_deg, d_new;
   int algo, al_sel, al_ident, rebuilds_in_row;
   int nz_sel, nz_static;
+  int est;                       // the Sec. 5 schedule: Delta-hat and binomial batches
+  int64_t period, rank_cursor;   // rounds per halving of Delta-hat; ranks of pi passed
+  int64_t batch_end;             // alive-list index that ends the round's batch
   unsigned long long t0, round_t0;
   unsigned long long ph_ns[8];
 };
@@ -304,6 +350,10 @@ struct K {
       c.rebuilds_in_row = 0;
       c.algo = vload(&C->algo);
       c.eps_ppm = vload(&C->eps_ppm);
+      c.est = c.algo >= 3;                // the Sec. 5 schedule
+      if (c.est) c.algo -= 2;
+      c.period = c.est ? sec5_period(c.n, c.max_deg, c.eps_ppm) : 0;
+      c.rank_cursor = 0;
       c.stats_cap = B.stats_cap;
       Plan& p = S->plan;
       p = Plan{};
@@ -334,13 +384,19 @@ struct K {
       const int64_t avail = c.al_len - c.cursor;
       const int64_t est = (int64_t)((double)k * (double)avail / (double)c.n_alive * 1.05) + 256;
       c.win_len = est < avail ? est : avail;
+      if (c.est) {
+        // Sec. 5: the whole window of the round's batch, every alive entry of it
+        c.k = 0;                          // set from the window's alive count
+        c.need = INT64_MAX / 4;
+        c.win_len = c.batch_end - c.cursor;
+      }
       c.r_edges = 0;
       C->act_pack = 0; C->new_pack = 0; C->blk_pack = 0;
       C->r_centers = 0; C->r_attached = 0; C->r_noncenter = 0; C->r_blocked = 0;
       C->r0 = -1;
       p.state = kRun;
-      p.k = k;
-      p.need = k;
+      p.k = c.k;
+      p.need = c.need;
       p.win_lo = c.win_lo;
       p.win_len = c.win_len;
       p.th = 0;
@@ -367,6 +423,18 @@ struct K {
         p.al_ident = c.al_ident;
         p.win_lo = c.cursor;
         p.win_len = c.al_len - c.cursor;
+      } else if (c.est) {
+        p.state = kDrawBatch;             // Sec. 5: draw the batch, no Delta
+        const int64_t dh = sec5_delta_hat(c.max_deg, c.period, c.round);
+        bool all;
+        const uint64_t thr = sec5_threshold(c.eps_ppm, dh, &all);
+        c.delta = (int32_t)dh;
+        p.win_len = c.n - c.rank_cursor;                            // trials
+        p.need = (int64_t)thr;                                      // threshold bits
+        p.take = all ? 1 : 0;
+        p.k = (int64_t)perm_key(vload(&C->seed) ^ 0x5851F42D4C957F2Dull, (uint64_t)c.round);   // stream seed
+        p.al_sel = c.al_sel;
+        p.al_ident = c.al_ident;
       } else if (c.nz_len == 0) {
         dec = 2;                          // every alive vertex is isolated: Delta = 0
       } else if (c.h_len == 0 || c.h_len > kInlineH) {
@@ -449,10 +517,63 @@ struct K {
       if (c.n_alive < 0) fail(kErrInternal);
       c.round = r + 1;
       c.rebuilds_in_row = 0;
-      if (c.round > c.n + 1) fail(kErrInternal);
+      if (!c.est && c.round > c.n + 1) fail(kErrInternal);   // Sec. 5 rounds may hold no active vertex
     }
     __syncthreads();
     co_decide_delta();
+  }
+
+  // ---------------- Sec. 5: the round's binomial batch ------------------------
+  // Every block counts its share of the round's draws below the threshold
+  // (plan: win_len trials, need = threshold bits, take = every trial
+  // succeeds, k = stream seed); the coordinator adds them up, moves the rank
+  // cursor past the batch, finds where the batch ends in the alive list and
+  // plans the round's single selection window.
+  __device__ bool draw_batch() {
+    const int64_t trials = P().win_len;
+    const uint64_t thr = (uint64_t)P().need, s = (uint64_t)P().k;
+    int64_t cnt = 0;
+    if (P().take) {
+      cnt = bid == 0 && threadIdx.x == 0 ? trials : 0;
+    } else {
+      for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < trials; j += (int64_t)G * blockDim.x)
+        cnt += sec5_draw(s, (uint64_t)j) < thr ? 1 : 0;
+    }
+    cnt = block_sum<int64_t>(cnt, S->scr);
+    if (threadIdx.x == 0) B.blk_a[bid] = cnt;
+    return sync(2, [&] {
+      const int64_t b = prefix_blocks();
+      Coord& c = co();
+      const int64_t end_rank = c.rank_cursor + b;
+      // first alive-list entry at or past end_rank (the list is rank-ordered)
+      int64_t end;
+      if (c.al_ident) {
+        end = end_rank < c.al_len ? end_rank : c.al_len;
+      } else {
+        int64_t lo = c.cursor, hi = c.al_len;
+        for (;;) {
+          const int64_t span = hi - lo;
+          if (span <= 0) break;
+          const int64_t step = (span + blockDim.x - 1) / blockDim.x;
+          const int64_t q = lo + (int64_t)threadIdx.x * step;
+          const bool below = q < hi && al_at(c.al_sel, 0, q).x < end_rank;
+          const int64_t f = __syncthreads_count(below);
+          if (step == 1) { lo += f; break; }
+          const int64_t nlo = f > 0 ? lo + (f - 1) * step + 1 : lo;
+          const int64_t nhi = lo + f * step < hi ? lo + f * step : hi;
+          lo = nlo;
+          hi = nhi;
+        }
+        end = lo;
+      }
+      if (threadIdx.x == 0) {
+        c.batch_end = end;
+        c.rank_cursor = end_rank;
+        if (end_rank > c.n) fail(kErrInternal);
+      }
+      __syncthreads();
+      plan_selection(c.delta);
+    });
   }
 
   // ---------------- alive-list compaction -----------------------------------
@@ -755,6 +876,7 @@ struct K {
             if (threadIdx.x == 0) {
               const int64_t need = co().need;
               S->plan.take = tot < need ? tot : need;
+              if (co().est) { co().k = tot; S->plan.k = tot; }   // Sec. 5: all of the window
             }
           }))
         return false;
@@ -798,11 +920,11 @@ struct K {
               Coord& c = co();
               Plan& p = S->plan;
               if (p.r0 < 0) p.r0 = vload(&C->r0);
-              const int64_t left = c.need - p.take;
+              const int64_t left = c.est ? 0 : c.need - p.take;
               c.need = left;
               p.need = left;
               if (left == 0) {
-                c.cursor = vload(&C->cursor_next);
+                c.cursor = c.est ? c.batch_end : vload(&C->cursor_next);
                 const unsigned long long pk = vload(&C->act_pack);
                 p.act_n = (int64_t)(pk >> kPackShift);
                 p.act_E = (int64_t)(pk & kPackEdgeMask);
@@ -1092,6 +1214,7 @@ struct K {
 __device__ void run_job(K& k, int algo) {
   Shared& S = *k.S;
   Ctl* C = k.C;
+  if (algo >= 3) algo -= 2;             // the Sec. 5 schedule: same rounds, C4 or ClusterWild!
   if (k.bid == 0 && threadIdx.x == 0) {
     for (int i = 0; i < 8; ++i) S.co.ph_ns[i] = 0;
     S.co.t0 = globaltimer_ns();
@@ -1112,6 +1235,10 @@ __device__ void run_job(K& k, int algo) {
     }
     if (S.plan.state == kScanH) {
       if (!k.heavy_scan()) goto out;
+      continue;
+    }
+    if (S.plan.state == kDrawBatch) {
+      if (!k.draw_batch()) goto out;
       continue;
     }
     if (!k.select(algo)) goto out;
@@ -1364,6 +1491,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
             C->err = 0;
             C->algo = algo;
             C->eps_ppm = eps_ppm;
+            C->seed = jobs[j].seed;
             C->mc = 0; C->mm = 0; C->pairs = 0;
             C->undecided = 0; C->h_pack = 0;
             S.plan.state = kRun;
@@ -1408,7 +1536,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
   }
 }
 
-__global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm) {
+__global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm, uint64_t seed) {
   const int64_t n = B.n;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
@@ -1423,6 +1551,7 @@ __global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm) {
     Ctl* C = B.ctl;
     C->algo = algo;
     C->eps_ppm = eps_ppm;
+    C->seed = seed;
     C->n_alive = n;
     C->done = n > 0 ? 0 : 1;
   }
@@ -1517,10 +1646,11 @@ int rounds_grid_size(int device) {
   return sms * per;
 }
 
-cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, int grid, cudaStream_t stream) {
+cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, uint64_t seed, int grid,
+                          cudaStream_t stream) {
   cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(Ctl), stream);
   if (e != cudaSuccess) return e;
-  k_init_state<<<grid, 256, 0, stream>>>(b, algo, eps_ppm);
+  k_init_state<<<grid, 256, 0, stream>>>(b, algo, eps_ppm, seed);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (b.n <= 0) return cudaSuccess;

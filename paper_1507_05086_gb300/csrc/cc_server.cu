@@ -272,7 +272,7 @@ int cc_server_create(size_t mem_budget, int32_t max_batch, cc_server** out) {
 int cc_server_submit(cc_server* sv, cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out,
                      int64_t* ticket) {
   if (!sv || !g || !ticket) return CC_ERR_INVALID_ARG;
-  if (algo != CC_ALGO_C4 && algo != CC_ALGO_CLUSTERWILD) return CC_ERR_INVALID_ARG;
+  if (algo < CC_ALGO_C4 || algo > CC_ALGO_CLUSTERWILD_EST) return CC_ERR_INVALID_ARG;
   if (!(eps > 0.0) || !(eps <= 1.0)) return CC_ERR_INVALID_ARG;
   const long long ppm = std::llround(eps * 1e6);
   if (ppm < 1 || ppm > 1000000) return CC_ERR_INVALID_ARG;

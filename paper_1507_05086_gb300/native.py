@@ -18,7 +18,10 @@ from . import build as _build
 
 C4 = 1
 CLUSTERWILD = 2
-ALGOS = {"c4": C4, "cw": CLUSTERWILD, "clusterwild": CLUSTERWILD, C4: C4, CLUSTERWILD: CLUSTERWILD}
+C4_EST = 3              # the same with the practical schedule of Sec. 5
+CLUSTERWILD_EST = 4
+ALGOS = {"c4": C4, "cw": CLUSTERWILD, "clusterwild": CLUSTERWILD, "c4-est": C4_EST, "cw-est": CLUSTERWILD_EST,
+         C4: C4, CLUSTERWILD: CLUSTERWILD, C4_EST: C4_EST, CLUSTERWILD_EST: CLUSTERWILD_EST}
 
 CC_DEVICE_PTRS = 2
 CC_OFFSETS_I32 = 4

@@ -320,3 +320,44 @@ def test_hubs_losing_degree_while_alive_match_oracle(cc, ora, gg):
                 for f in STAT_FIELDS:
                     assert np.array_equal(st[f], ost[f]), (algo, eps, f)
                 assert d == ora.disagreements(g.off, g.col, olab)
+
+
+@pytest.mark.parametrize("algo,a", [("c4-est", 1), ("cw-est", 2)])
+@pytest.mark.parametrize("eps", [0.1, 0.5, 1.0])
+def test_sec5_schedule_matches_oracle(cc, ora, gg, algo, a, eps):
+    """The practical schedule of Sec. 5 (Delta-hat halving, binomial batches
+    over the unprocessed suffix of pi): labels, rounds and every round's
+    statistics equal the oracle's; C4 still equals KwikCluster."""
+    graphs = small_graphs(gg, 5) + [gg.from_edges(9, np.zeros(0, np.int32), np.zeros(0, np.int32))]
+    for gi, g in enumerate(graphs):
+        with cc.Graph(g.off, g.col) as graph:
+            for seed in (0, 7, 2**45 + 11):
+                order = ora.permutation(g.n, seed)
+                olab, orr, _, ost = ora.rounds_bsp(g.off, g.col, order, a, eps, seed, stats_cap=1_000_000)
+                lab, r, d, st = graph.cluster(algo, eps, seed, stats_cap=1_000_000)
+                assert np.array_equal(lab, olab), (gi, seed)
+                assert r == orr
+                for f in STAT_FIELDS:
+                    assert np.array_equal(st[f], ost[f]), (gi, seed, f)
+                assert d == ora.disagreements(g.off, g.col, olab)
+                if a == 1:
+                    assert np.array_equal(lab, ora.kwik(g.off, g.col, order))
+
+
+def test_sec5_schedule_larger_graphs_and_batches(cc, ora, gg):
+    """R-MAT and planted graphs through the whole grid and through the
+    batched engine (one block and eight-block teams)."""
+    graphs = [gg.rmat(15, 8, seed=3), gg.planted_partition(n=60_000, q=150, seed=4, noise=80_000)]
+    for g in graphs:
+        with cc.Graph(g.off, g.col) as graph:
+            for algo, a in (("cw-est", 2), ("c4-est", 1)):
+                seed = 99
+                order = ora.permutation(g.n, seed)
+                olab, orr, _, _ = ora.rounds_bsp(g.off, g.col, order, a, 0.5, seed)
+                lab, r, d = graph.cluster(algo, 0.5, seed)
+                assert np.array_equal(lab, olab) and r == orr
+                D, R = cc.batch_jobs([graph], algo, 0.5, np.array([seed], np.uint64), 2)
+                for j in range(2):
+                    o2 = ora.permutation(g.n, seed + j)
+                    l2, r2, _, _ = ora.rounds_bsp(g.off, g.col, o2, a, 0.5, seed + j)
+                    assert R[0, j] == r2 and D[0, j] == ora.disagreements(g.off, g.col, l2)
