@@ -9,6 +9,16 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(scope="module")
+def cc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1507_05086_gb300 as cc
+    cc.load()
+    return cc
+
+
 def test_quality_study_matches_oracle(cc, ora, gg):
     import quality
     g = gg.erdos_renyi(10_000, 20.0 / 9_999.0, seed=0)
