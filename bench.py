@@ -45,6 +45,7 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-graphs", type=int, default=256,
                    help="Chung-Lu graphs in the batched-jobs measurement (0 = skip)")
+    p.add_argument("--sec5", type=int, default=1, help="also time the Sec. 5 schedule once per algorithm (0 = skip)")
     p.add_argument("--serve-seconds", type=float, default=2.0,
                    help="length of the Poisson arrival stream for the serving measurement (0 = skip)")
     return p.parse_args(argv)
@@ -426,6 +427,19 @@ def run_ours(args):
                "what": "per step: cc_graph_create from pinned host CSR (copy + validation), one C4 and one "
                        "ClusterWild! cc_cluster with labels to pinned host memory, cc_graph_destroy"}
 
+    # the practical schedule of Sec. 5 (Delta-hat halving, binomial batches) on
+    # the same graph, one clustering each: a comparison, not part of a step
+    sec5 = None
+    if rank == 0 and args.sec5:
+        sec5 = {}
+        for a in algos:
+            graph.cluster(a + "-est", args.eps, 4242, labels_out=labels)
+            pm, rm, lm = graph.last_timings()
+            _, r, d = graph.cluster(a + "-est", args.eps, 4243, labels_out=labels)
+            pm, rm, lm = graph.last_timings()
+            sec5[a + "-est"] = {"ms_per_clustering": pm + rm + lm, "rounds_kernel_ms": rm, "rounds": r,
+                                "disagreements": d, "edges_per_s": m / ((pm + rm + lm) / 1e3)}
+
     batch = serve = None
     if rank == 0 and (args.batch_graphs > 0 or args.serve_seconds > 0):
         bgs = batch_workload(max(args.batch_graphs, 64))
@@ -468,6 +482,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "batch": batch,
             "serve": serve,
+            "sec5_schedule": sec5,
         }
         print(json.dumps(line), flush=True)
     graph.close()
