@@ -159,7 +159,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
 }
 constexpr int kLbsW = 32 * kLbsK;
 #ifndef CC_LBS_BATCHES
-#define CC_LBS_BATCHES 8
+#define CC_LBS_BATCHES 4
 #endif
 constexpr int kLbsBatches = CC_LBS_BATCHES;   // batches per chunk of a long walk
 
