@@ -108,6 +108,7 @@ struct RoundBuffers {
   int64_t* b_d;
   int64_t* blk_a;              // per-block scratch
   int64_t* blk_b;
+  unsigned long long* desc;    // per-block scan descriptors of the selection (decoupled look-back)
   RoundStat* stats;
   int64_t stats_cap;
   Ctl* ctl;

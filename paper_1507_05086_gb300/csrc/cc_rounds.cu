@@ -12,10 +12,11 @@
 // Per-vertex state: one 32-bit word st[v]
 //   alive ............ kAlive | residual degree
 //   clustered ........ kLab + center rank
-//   active this round  kActive / kActCenter / kActNon (undecided or
-//                      ClusterWild! center / C4 center / C4 non-center)
-// An active's rank is kept in arank[v]; a center keeps the active marker until
-// the next round starts, then takes kLab + its own rank.
+//   active ............ kActive / kActCenter / kActNon (undecided or
+//                       ClusterWild! center / C4 center / C4 non-center)
+// An active's rank is kept in arank[v].  A center keeps its active marker for
+// good (its label is its own rank, arank); the actives of the current round
+// are the ones whose rank is >= r0, the round's first active rank.
 //
 // Attachment (createCluster, concurrency rule 2): a center of rank r lowers
 // st[u] with atomicMin(kLab + r).  Alive words compare above every label and
@@ -838,27 +839,86 @@ struct K {
     }
   }
 
+  // Decoupled look-back (one pass instead of count, barrier, emit): block bid
+  // of the team publishes its alive count (flag 1) and then its inclusive
+  // prefix (flag 2) in desc[bid], tagged with the barrier epoch; warp 0
+  // reads the 32 closest predecessors at a time and sums aggregates back to
+  // the nearest inclusive prefix.  Returns the exclusive prefix of this block
+  // (every thread of warp 0; block 0 returns 0).  Every wait is bounded.
+  static constexpr unsigned long long kDescVal = (1ull << 38) - 1;
+  __device__ __forceinline__ unsigned long long pack_desc(unsigned flag, long long v) const {
+    return ((unsigned long long)(epoch & 0xFFFFFFu) << 40) | ((unsigned long long)flag << 38) |
+           ((unsigned long long)v & kDescVal);
+  }
+  __device__ long long lookback(long long mine) {
+    const int lane = threadIdx.x & 31;
+    volatile unsigned long long* d = B.desc;
+    if (bid == 0) {
+      if (lane == 0) d[0] = pack_desc(2, mine);
+      return 0;
+    }
+    if (lane == 0) d[bid] = pack_desc(1, mine);
+    const unsigned tag = epoch & 0xFFFFFFu;
+    long long excl = 0;
+    int64_t pos = (int64_t)bid - 1;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+      const int64_t q = pos - lane;
+      unsigned long long x = q >= 0 ? d[q] : pack_desc(2, 0);
+      bool ready = (unsigned)(x >> 40) == tag && ((x >> 38) & 3u) != 0;
+      unsigned spins = 0;
+      while (!__all_sync(FULL, ready)) {
+        if (!ready) {
+          x = d[q];
+          ready = (unsigned)(x >> 40) == tag && ((x >> 38) & 3u) != 0;
+        }
+        if ((++spins & 63) == 0) {
+          const bool give_up = ld_volatile_int(&C->err) != kOk || globaltimer_ns() - t0 > kBarrierLimitNs;
+          if (__any_sync(FULL, give_up)) {
+            if (lane == 0) atomicCAS(&C->err, kOk, kErrTimeout);
+            return excl;
+          }
+        }
+      }
+      // the closest predecessor with an inclusive prefix ends the walk
+      const unsigned incl = __ballot_sync(FULL, ((x >> 38) & 3u) == 2u);
+      const int stop = incl ? __ffs(incl) - 1 : 31;
+      long long v = lane <= stop ? (long long)(x & kDescVal) : 0;
+      v = warp_sum(v);
+      excl += v;
+      if (incl) break;
+      pos -= 32;
+    }
+    if (lane == 0) d[bid] = pack_desc(2, excl + mine);
+    return excl;
+  }
+
   __device__ bool select(int algo) {
     for (;;) {
       const int sel = P().al_sel, ident = P().al_ident;
       const int64_t wlo = P().win_lo, wlen = P().win_len;
       int64_t s, e;
       slice(wlo, wlen, &s, &e);
-      // C4: the previous round's centers still hold an active marker: give
-      // them their labels (own rank) before this round marks new actives.
-      // ClusterWild! centers keep kActive for good: no pass tells an old
-      // center from a current active by its word alone (they are filtered by
-      // the removal tag, and a center's label is its arank)
-      if (P().r0 < 0 && algo == kAlgoC4) {
-        const int64_t pn = P().act_n;
-        for (int64_t j = (int64_t)bid * blockDim.x + threadIdx.x; j < pn; j += (int64_t)G * blockDim.x) {
-          const int32_t v = ldcg(B.act_v + j);
-          if (is_active(ldcg(B.st + v))) B.st[v] = kLab + (uint32_t)ldcg(B.act_r + j);
-        }
+      // Centers keep their active marker for good (a center's label is its
+      // arank): an active of this round is told from an earlier round's
+      // center by its rank, which is >= r0, the round's first active rank.
+      // count this block's alive entries (the first tile stays in registers)
+      const int64_t tile = (int64_t)blockDim.x * kScanU;
+      int2 a0[kScanU];
+      bool alive0[kScanU];
+      int64_t mine0 = 0;
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = s + (int64_t)threadIdx.x * kScanU + q;
+        a0[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
       }
-      // S1: alive count per block
-      int64_t cnt = 0;
-      for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        alive0[q] = a0[q].y >= 0 && rtag_of(B.rtag, a0[q].y) == 0;
+        mine0 += alive0[q] ? 1 : 0;
+      }
+      int64_t cnt = mine0;
+      for (int64_t base = s + tile; base < e; base += tile) {
         int2 a[kScanU];
 #pragma unroll
         for (int q = 0; q < kScanU; ++q) {
@@ -870,55 +930,64 @@ struct K {
           cnt += (a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0) ? 1 : 0;
       }
       cnt = block_sum<int64_t>(cnt, S->scr);
-      if (threadIdx.x == 0) B.blk_a[bid] = cnt;
-      if (!sync(2, [&] {
-            const int64_t tot = prefix_blocks();
-            if (threadIdx.x == 0) {
-              const int64_t need = co().need;
-              S->plan.take = tot < need ? tot : need;
-              if (co().est) { co().k = tot; S->plan.k = tot; }   // Sec. 5: all of the window
-            }
-          }))
-        return false;
-      // S2: emit the first `take` alive entries of the window
-      const int64_t take = P().take, need = P().need;
+      // this block's first alive entry is number `run` of the window
+      if (threadIdx.x < 32) {
+        const long long ex = lookback(cnt);
+        if (threadIdx.x == 0) S->bcast[2] = ex;
+      }
+      __syncthreads();
+      int64_t run = S->bcast[2];
+      __syncthreads();
+      // emit the alive entries of the window numbered below `need`
+      const int64_t need = P().need;
       const bool first_window = P().r0 < 0;
-      int64_t run = ldcg(B.blk_a + bid);
-      if (run < take) {
-        for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+      if (run < need) {
+        for (int64_t base = s; base < e; base += tile) {
           int2 a[kScanU];
           bool alive[kScanU];
           int64_t mine = 0;
+          if (base == s) {
 #pragma unroll
-          for (int q = 0; q < kScanU; ++q) {
-            const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
-            a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
-          }
+            for (int q = 0; q < kScanU; ++q) {
+              a[q] = a0[q];
+              alive[q] = alive0[q];
+            }
+            mine = mine0;
+          } else {
 #pragma unroll
-          for (int q = 0; q < kScanU; ++q) {
-            alive[q] = a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0;
-            mine += alive[q] ? 1 : 0;
+            for (int q = 0; q < kScanU; ++q) {
+              const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+              a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
+            }
+#pragma unroll
+            for (int q = 0; q < kScanU; ++q) {
+              alive[q] = a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0;
+              mine += alive[q] ? 1 : 0;
+            }
           }
           int64_t tot;
           int64_t g = run + block_exclusive_sum<int64_t>(mine, S->scr, &tot);
           bool want[kScanU];
 #pragma unroll
           for (int q = 0; q < kScanU; ++q) {
-            want[q] = alive[q] && g < take;
+            want[q] = alive[q] && g < need;
             if (want[q] && g == 0 && first_window) C->r0 = a[q].x;
-            if (want[q] && take == need && g == take - 1)
-              C->cursor_next = base + (int64_t)threadIdx.x * kScanU + q + 1;
+            if (want[q] && g == need - 1) C->cursor_next = base + (int64_t)threadIdx.x * kScanU + q + 1;
             g += alive[q] ? 1 : 0;
           }
           emit_actives(a, want, algo);
           run += tot;
-          if (run >= take) break;           // uniform across the block
+          if (run >= need) break;           // uniform across the block
         }
       }
       if (!sync(3, [&] {
             if (threadIdx.x == 0) {
               Coord& c = co();
               Plan& p = S->plan;
+              // the last block's inclusive prefix: the window's alive count
+              const int64_t total = (int64_t)(ldcg(B.desc + (G - 1)) & kDescVal);
+              p.take = total < c.need ? total : c.need;
+              if (c.est) { c.k = total; p.k = total; }   // Sec. 5: all of the window
               if (p.r0 < 0) p.r0 = vload(&C->r0);
               const int64_t left = c.est ? 0 : c.need - p.take;
               c.need = left;
@@ -1029,7 +1098,10 @@ struct K {
         // an earlier active neighbour: v must wait (isCenter); actives carry
         // this round's tag
         if (rtag_of(B.rtag, u[q]) != (uint32_t)P().tag) continue;
-        if (is_active(ldcg(B.st + u[q])) && ldcg(B.arank + u[q]) < L.vtx(q)) B.blk_flag[L.item(q)] = 1;
+        if (is_active(ldcg(B.st + u[q]))) {
+          const int32_t ru = ldcg(B.arank + u[q]);
+          if (ru >= P().r0 && ru < L.vtx(q)) B.blk_flag[L.item(q)] = 1;
+        }
       }
     }, B.act_d, B.act_r);
   }
@@ -1075,7 +1147,8 @@ struct K {
         const int32_t u = __ldg(B.col + L.edge(i) + ldcg(B.b_d + L.item(i)));
         if (rtag_of(B.rtag, u) != (uint32_t)P().tag) continue;     // not an active of this round
         const uint32_t x = ldcg(B.st + u);
-        if (is_active(x) && ldcg(B.arank + u) < rv) {
+        const int32_t ru = is_active(x) ? ldcg(B.arank + u) : -1;
+        if (ru >= P().r0 && ru < rv) {
           if (x == kActCenter) B.hit_c[L.item(i)] = 1;
           else if (x == kActive) B.hit_p[L.item(i)] = 1;
         }
@@ -1122,7 +1195,8 @@ struct K {
           if (ldcg(B.st + v) == kActCenter) {
             push = true;
           } else if (x == kActCenter) {
-            atomicMin(B.pull + L.item(i), ldcg(B.arank + u));
+            const int32_t ru = ldcg(B.arank + u);
+            if (ru >= P().r0) atomicMin(B.pull + L.item(i), ru);   // a center of this round
           }
         }
         attach_one(push, u, r, x);
@@ -1318,6 +1392,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ 
   Shared& S = *reinterpret_cast<Shared*>(smem_raw);
   K k{B, B.ctl, &S, gridDim.x, blockIdx.x, 0u, Tally{0, 0, 0, 0, 0}};
   if ((threadIdx.x & 31) == 0) S.u.w.app[threadIdx.x >> 5].n = 0;
+  // look-back descriptors of an earlier launch could carry the same epochs:
+  // clear this block's before the first barrier
+  if (threadIdx.x == 0) B.desc[blockIdx.x] = 0;
   __syncthreads();
   run_job(k, vload(&B.ctl->algo));
 }
@@ -1486,6 +1563,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
     // zero the permutation counters, reset the control block (not the barrier counters)
     const int64_t zn = 2 * (int64_t)kPermMaxBuckets + 2;
     for (int64_t i = (int64_t)k.bid * blockDim.x + threadIdx.x; i < zn; i += (int64_t)G * blockDim.x) rb.pcnt[i] = 0;
+    if (threadIdx.x == 0) rb.desc[k.bid] = 0;   // look-back descriptors of an earlier launch
     if (!k.sync(7, [&] {
           if (threadIdx.x == 0) {
             C->err = 0;
@@ -1600,7 +1678,7 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   b += 3 * align_up(nn);                 // blk_flag, hit_c, hit_p
   b += align_up(4 * nn);                 // pull
   b += align_up(4 * nn) + 2 * align_up(8 * nn);       // b_j, b_e, b_d
-  b += 2 * align_up(8 * ((size_t)grid + 1));          // blk_a, blk_b
+  b += 3 * align_up(8 * ((size_t)grid + 1));          // blk_a, blk_b, desc
   return b;
 }
 
@@ -1634,6 +1712,7 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   B->b_d = reinterpret_cast<int64_t*>(take(8 * nn));
   B->blk_a = reinterpret_cast<int64_t*>(take(8 * ((size_t)grid + 1)));
   B->blk_b = reinterpret_cast<int64_t*>(take(8 * ((size_t)grid + 1)));
+  B->desc = reinterpret_cast<unsigned long long*>(take(8 * ((size_t)grid + 1)));
 }
 
 int rounds_grid_size(int device) {
