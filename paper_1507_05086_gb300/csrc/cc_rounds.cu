@@ -166,6 +166,7 @@ struct Shared {
   int dec;
   int64_t scr[33];
   int64_t bcast[8];
+  unsigned long long tal[5];     // round tallies of the block (flushed at round end)
   union {
     struct {
       LbsWarp lbs[kWarps];
@@ -813,9 +814,10 @@ struct K {
       }
     }
     // one atomic per block and tile on the packed list counter
-    int64_t cnt_tot, e_tot;
-    const int64_t jx = block_exclusive_sum<int64_t>(nl, S->scr, &cnt_tot);
-    const int64_t ex = block_exclusive_sum<int64_t>(el, S->scr, &e_tot);
+    int64_t tot;
+    const int64_t pkx = block_exclusive_sum<int64_t>((nl << 40) | el, S->scr, &tot);
+    const int64_t jx = pkx >> 40, ex = pkx & ((1ll << 40) - 1);
+    const int64_t cnt_tot = tot >> 40, e_tot = tot & ((1ll << 40) - 1);
     if (cnt_tot == 0) return;
     if (threadIdx.x == 0) {
       const unsigned long long old =
@@ -839,57 +841,41 @@ struct K {
     }
   }
 
-  // Decoupled look-back (one pass instead of count, barrier, emit): block bid
-  // of the team publishes its alive count (flag 1) and then its inclusive
-  // prefix (flag 2) in desc[bid], tagged with the barrier epoch; warp 0
-  // reads the 32 closest predecessors at a time and sums aggregates back to
-  // the nearest inclusive prefix.  Returns the exclusive prefix of this block
-  // (every thread of warp 0; block 0 returns 0).  Every wait is bounded.
+  // Look-back over the team (one pass instead of count, barrier, emit):
+  // block bid publishes its alive count in desc[bid], tagged with the barrier
+  // epoch; thread q of the block waits for the counts of predecessors q,
+  // q + blockDim.x, ... and the block sums them (a single round of loads
+  // while the team has at most blockDim.x blocks).  The last block also
+  // stores the window's total in desc[G] for the coordinator.  A cleared
+  // descriptor (flag 0) is never taken for a count, whatever the epoch.
+  // Returns this block's exclusive prefix to every thread; every wait is
+  // bounded.
   static constexpr unsigned long long kDescVal = (1ull << 38) - 1;
   __device__ __forceinline__ unsigned long long pack_desc(unsigned flag, long long v) const {
     return ((unsigned long long)(epoch & 0xFFFFFFu) << 40) | ((unsigned long long)flag << 38) |
            ((unsigned long long)v & kDescVal);
   }
   __device__ long long lookback(long long mine) {
-    const int lane = threadIdx.x & 31;
     volatile unsigned long long* d = B.desc;
-    if (bid == 0) {
-      if (lane == 0) d[0] = pack_desc(2, mine);
-      return 0;
-    }
-    if (lane == 0) d[bid] = pack_desc(1, mine);
+    if (threadIdx.x == 0) d[bid] = pack_desc(1, mine);
     const unsigned tag = epoch & 0xFFFFFFu;
-    long long excl = 0;
-    int64_t pos = (int64_t)bid - 1;
+    long long v = 0;
     const uint64_t t0 = globaltimer_ns();
-    for (;;) {
-      const int64_t q = pos - lane;
-      unsigned long long x = q >= 0 ? d[q] : pack_desc(2, 0);
-      bool ready = (unsigned)(x >> 40) == tag && ((x >> 38) & 3u) != 0;
+    for (int64_t q = threadIdx.x; q < (int64_t)bid; q += blockDim.x) {
+      unsigned long long x = d[q];
       unsigned spins = 0;
-      while (!__all_sync(FULL, ready)) {
-        if (!ready) {
-          x = d[q];
-          ready = (unsigned)(x >> 40) == tag && ((x >> 38) & 3u) != 0;
+      while ((unsigned)(x >> 40) != tag || ((x >> 38) & 3u) == 0) {
+        if ((++spins & 63) == 0 && (ld_volatile_int(&C->err) != kOk || globaltimer_ns() - t0 > kBarrierLimitNs)) {
+          atomicCAS(&C->err, kOk, kErrTimeout);
+          x = 0;
+          break;
         }
-        if ((++spins & 63) == 0) {
-          const bool give_up = ld_volatile_int(&C->err) != kOk || globaltimer_ns() - t0 > kBarrierLimitNs;
-          if (__any_sync(FULL, give_up)) {
-            if (lane == 0) atomicCAS(&C->err, kOk, kErrTimeout);
-            return excl;
-          }
-        }
+        x = d[q];
       }
-      // the closest predecessor with an inclusive prefix ends the walk
-      const unsigned incl = __ballot_sync(FULL, ((x >> 38) & 3u) == 2u);
-      const int stop = incl ? __ffs(incl) - 1 : 31;
-      long long v = lane <= stop ? (long long)(x & kDescVal) : 0;
-      v = warp_sum(v);
-      excl += v;
-      if (incl) break;
-      pos -= 32;
+      v += (long long)(x & kDescVal);
     }
-    if (lane == 0) d[bid] = pack_desc(2, excl + mine);
+    const long long excl = block_sum<int64_t>(v, S->scr);
+    if (threadIdx.x == 0 && bid == G - 1) d[G] = pack_desc(2, excl + mine);
     return excl;
   }
 
@@ -918,26 +904,20 @@ struct K {
         mine0 += alive0[q] ? 1 : 0;
       }
       int64_t cnt = mine0;
-      for (int64_t base = s + tile; base < e; base += tile) {
-        int2 a[kScanU];
+      for (int64_t base = s + tile; base < e; base += 2 * tile) {
+        int2 a[2 * kScanU];
 #pragma unroll
-        for (int q = 0; q < kScanU; ++q) {
-          const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+        for (int q = 0; q < 2 * kScanU; ++q) {
+          const int64_t i = base + (int64_t)q * blockDim.x + threadIdx.x;
           a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
         }
 #pragma unroll
-        for (int q = 0; q < kScanU; ++q)
+        for (int q = 0; q < 2 * kScanU; ++q)
           cnt += (a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0) ? 1 : 0;
       }
       cnt = block_sum<int64_t>(cnt, S->scr);
       // this block's first alive entry is number `run` of the window
-      if (threadIdx.x < 32) {
-        const long long ex = lookback(cnt);
-        if (threadIdx.x == 0) S->bcast[2] = ex;
-      }
-      __syncthreads();
-      int64_t run = S->bcast[2];
-      __syncthreads();
+      int64_t run = lookback(cnt);
       // emit the alive entries of the window numbered below `need`
       const int64_t need = P().need;
       const bool first_window = P().r0 < 0;
@@ -985,7 +965,7 @@ struct K {
               Coord& c = co();
               Plan& p = S->plan;
               // the last block's inclusive prefix: the window's alive count
-              const int64_t total = (int64_t)(ldcg(B.desc + (G - 1)) & kDescVal);
+              const int64_t total = (int64_t)(ldcg(B.desc + G) & kDescVal);
               p.take = total < c.need ? total : c.need;
               if (c.est) { c.k = total; p.k = total; }   // Sec. 5: all of the window
               if (p.r0 < 0) p.r0 = vload(&C->r0);
@@ -1271,13 +1251,22 @@ struct K {
 
   // Reduce the round tallies of this block into the control block.
   __device__ void flush_round_tallies() {
-    const long long v[5] = {t.centers, t.attached, t.noncenter, t.blocked, (long long)t.mm};
-    long long* dst[5] = {&C->r_centers, &C->r_attached, &C->r_noncenter, &C->r_blocked,
-                         reinterpret_cast<long long*>(&C->mm)};
+    long long v[5] = {t.centers, t.attached, t.noncenter, t.blocked, (long long)t.mm};
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const long long s = block_sum<int64_t>(v[i], S->scr);
-      if (threadIdx.x == 0 && s != 0) atomicAdd(reinterpret_cast<unsigned long long*>(dst[i]), (unsigned long long)s);
+    for (int i = 0; i < 5; ++i) v[i] = warp_sum(v[i]);
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+      for (int i = 0; i < 5; ++i)
+        if (v[i]) atomicAdd(&S->tal[i], (unsigned long long)v[i]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 5) {
+      unsigned long long* dst[5] = {reinterpret_cast<unsigned long long*>(&C->r_centers),
+                                    reinterpret_cast<unsigned long long*>(&C->r_attached),
+                                    reinterpret_cast<unsigned long long*>(&C->r_noncenter),
+                                    reinterpret_cast<unsigned long long*>(&C->r_blocked), &C->mm};
+      const unsigned long long x = S->tal[threadIdx.x];
+      if (x) { atomicAdd(dst[threadIdx.x], x); S->tal[threadIdx.x] = 0; }
     }
     t = Tally{0, 0, 0, 0, 0};
   }
@@ -1392,6 +1381,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ 
   Shared& S = *reinterpret_cast<Shared*>(smem_raw);
   K k{B, B.ctl, &S, gridDim.x, blockIdx.x, 0u, Tally{0, 0, 0, 0, 0}};
   if ((threadIdx.x & 31) == 0) S.u.w.app[threadIdx.x >> 5].n = 0;
+  if (threadIdx.x < 5) S.tal[threadIdx.x] = 0;
   // look-back descriptors of an earlier launch could carry the same epochs:
   // clear this block's before the first barrier
   if (threadIdx.x == 0) B.desc[blockIdx.x] = 0;
@@ -1578,6 +1568,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
       break;
     if (!team_permutation(k, jobs[j].seed)) break;
     if ((threadIdx.x & 31) == 0) S.u.w.app[threadIdx.x >> 5].n = 0;
+    if (threadIdx.x < 5) S.tal[threadIdx.x] = 0;
     __syncthreads();
     run_job(k, algo);
     if (S.plan.state == kAbort) {
