@@ -214,7 +214,11 @@ __device__ __forceinline__ int64_t warp_upper_bound(const int64_t* a, int64_t n,
 // of kLbsW virtual edges.  A batch that lies inside one item (a long row)
 // needs none of the per-item loads: the warp keeps the range, delta and
 // vertex of its current item, taken from the previous batch's loads, and
-// only a batch that crosses an item boundary loads and scans item starts.
+// only a batch that crosses an item boundary loads and scans item starts,
+// in groups of 32 items: a group is loaded only while the previous one ends
+// inside the batch, so a batch spanning a few rows costs one group, not
+// kLbsK (every item owns at least one edge, so kLbsK groups always suffice,
+// and the item after the batch's last one is always among those loaded).
 // With vmap, the per-item payload is vmap[vtx[j]] - vsub instead of vtx[j]
 // (one load per item, not per edge).
 //
@@ -263,13 +267,20 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
     int64_t s[kLbsK];
 #pragma unroll
     for (int t = 0; t < kLbsK; ++t) {
+      s[t] = INT64_MAX;
+      ws->mark[lane + 32 * t] = -1;
+    }
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      // a group of 32 items is needed while the previous group's last item
+      // starts inside the batch or at its end
+      if (t > 0 && __shfl_sync(FULL, s[t - 1], 31) > base + kLbsW) break;
       const int64_t jj = j0 + lane + 32 * t;
       const bool in = jj < nitems;
       s[t] = in ? ldcg(epos + jj) : INT64_MAX;
       // per-item data loads issue together with the start offsets
       if (delta) ws->dlt[lane + 32 * t] = in ? ldcg(delta + jj) : 0;
       if (vtx) ws->vtx[lane + 32 * t] = in ? ldcg(vtx + jj) : 0;
-      ws->mark[lane + 32 * t] = -1;
     }
     if (lane == 0) ws->next = -1;
     __syncwarp();

@@ -200,8 +200,11 @@ struct K {
   __device__ __forceinline__ void lbs(const int64_t* epos, int64_t nitems, int64_t E, F&& f,
                                       const int64_t* delta = nullptr, const int32_t* vtx = nullptr,
                                       const uint32_t* vmap = nullptr, uint32_t vsub = 0) {
-    // every walk with a delta array walks CSR rows: stream them ahead
-    lbs_for_each_in(((int64_t)bid * blockDim.x + threadIdx.x) >> 5, ((int64_t)G * blockDim.x) >> 5, epos, nitems,
+    // every walk with a delta array walks CSR rows: stream them ahead.
+    // Warps are numbered across the blocks first (warp w of block b is
+    // w * G + b), so a short walk spreads over every SM instead of the
+    // first few blocks.
+    lbs_for_each_in((int64_t)(threadIdx.x >> 5) * G + bid, ((int64_t)G * blockDim.x) >> 5, epos, nitems,
                     E, lbs_ws(), f, delta, vtx, 0, vmap, vsub, delta ? B.col : nullptr);
   }
 
