@@ -77,6 +77,17 @@ extern "C" {
  * cc_round_stats.delta then reports Delta-hat_i and .k the active count. */
 #define CC_ALGO_C4_EST          3
 #define CC_ALGO_CLUSTERWILD_EST 4
+/* C4 with no rounds at all: the asynchronous execution of Alg. 3 with
+ * attemptCluster.  Vertices are decided in pi order by whichever warp holds
+ * them; a vertex waits (bounded) only for its undecided earlier-ranked
+ * neighbours, and becomes a center iff none of them is one.  The output
+ * equals KwikCluster(pi) and CC_ALGO_C4 (Sec. 4).  eps is checked but
+ * unused; rounds_out is 0; cc_cluster_ex writes one statistics record for
+ * the whole run (n_alive = k = removed = n, delta = the maximum degree,
+ * centers, blocked = vertices that waited on an undecided neighbour,
+ * edges = adjacency entries read by the decisions, ns = 0).
+ * cc_cluster / cc_cluster_ex only (not the batch or server entry points). */
+#define CC_ALGO_C4_ASYNC        5
 
 /* ---- cc_graph_create flags ----------------------------------------------- */
 #define CC_DEVICE_PTRS  2u   /* row_offsets/col_idx are device pointers, adopted by
@@ -133,8 +144,8 @@ int cc_permutation(cc_graph* g, uint64_t seed, int32_t* order_out);
 
 /*
  * cc_cluster -- one full clustering (Alg. 2) of graph g.
- *   algo               CC_ALGO_C4, CC_ALGO_CLUSTERWILD, CC_ALGO_C4_EST or
- *                      CC_ALGO_CLUSTERWILD_EST.
+ *   algo               CC_ALGO_C4, CC_ALGO_CLUSTERWILD, CC_ALGO_C4_EST,
+ *                      CC_ALGO_CLUSTERWILD_EST or CC_ALGO_C4_ASYNC.
  *   eps                0 < eps <= 1 (Sec. 3 assumes eps <= 1).
  *   seed               selects pi.
  *   labels_out         int32[n], host or device memory: the center vertex id
@@ -147,7 +158,8 @@ int cc_cluster(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels
                int32_t* rounds_out, int64_t* disagreements_out);
 
 /* cc_cluster plus per-round statistics: the first min(rounds, stats_cap)
- * rounds are written to stats (host memory); *stats_len = rounds. */
+ * rounds are written to stats (host memory); *stats_len = rounds
+ * (CC_ALGO_C4_ASYNC: one record for the whole run, *stats_len = 1). */
 int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out,
                   int32_t* rounds_out, int64_t* disagreements_out, cc_round_stats* stats,
                   int32_t stats_cap, int32_t* stats_len);
@@ -171,7 +183,8 @@ int cc_disagreements(cc_graph* g, const int32_t* labels, int64_t* out);
  *                            best permutation (lowest D, ties to lowest j), its
  *                            disagreements and its round count.
  * Jobs run concurrently on the device; each result is the same as the
- * corresponding single cc_cluster call.
+ * corresponding single cc_cluster call.  algo: CC_ALGO_C4 ..
+ * CC_ALGO_CLUSTERWILD_EST (CC_ALGO_C4_ASYNC is CC_ERR_INVALID_ARG here).
  */
 int cc_batch_run(cc_graph* const* gs, int32_t count, int algo, double eps,
                  const uint64_t* seeds, int32_t k_perms, int32_t* const* labels_out,
@@ -242,7 +255,8 @@ int cc_disagreements_static(int64_t n, const int64_t* row_offsets, const int32_t
  * while others run are admitted and overlap with them.  Graphs stay resident
  * (they are the caller's, and must outlive their requests); graphs above 2^16
  * vertices run on the whole GPU one at a time.  The result of a request is
- * exactly that of cc_cluster with the same arguments.
+ * exactly that of cc_cluster with the same arguments.  algo: CC_ALGO_C4 ..
+ * CC_ALGO_CLUSTERWILD_EST (CC_ALGO_C4_ASYNC is CC_ERR_INVALID_ARG here).
  *   mem_budget   bytes of device memory for batch scratch (a request whose
  *                scratch alone exceeds it fails with CC_ERR_OOM).
  *   max_batch    largest number of requests per launch.

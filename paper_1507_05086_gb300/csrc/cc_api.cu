@@ -1,6 +1,6 @@
 // cc_api.cu -- the C ABI (include/cc.h): argument checks, device memory,
 // launches and result transfer.  All computation happens in the kernels of
-// cc_perm.cu, cc_rounds.cu and cc_objective.cu.
+// cc_perm.cu, cc_rounds.cu, cc_async.cu and cc_objective.cu.
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/cc.h"
+#include "cc_async.h"
 #include "cc_graph_impl.h"
 #include "cc_internal.h"
 
@@ -133,6 +134,13 @@ int ensure_cluster_ws(cc_graph* g) {
 
 int ensure_labels_tmp(cc_graph* g) {
   if (!g->labels_tmp) CC_TRY(dalloc(&g->labels_tmp, 4 * (size_t)g->n, g->stream));
+  return CC_OK;
+}
+
+int ensure_objective_ws(cc_graph* g) {
+  if (!g->obj_ws) CC_TRY(dalloc(&g->obj_ws, objective_workspace_bytes(g->n), g->stream));
+  if (!g->obj_out) CC_TRY(dalloc(&g->obj_out, 4 * sizeof(unsigned long long), g->stream));
+  if (!g->obj_host) CC_TRY(cudaMallocHost(&g->obj_host, 4 * sizeof(unsigned long long)));
   return CC_OK;
 }
 
@@ -343,10 +351,77 @@ int cc_permutation(cc_graph* g, uint64_t seed, int32_t* order_out) {
   return status_of_device_err(err);
 }
 
+// C4 without rounds (Alg. 3): permutation, the asynchronous decisions and
+// pushes, labels, then the objective from the labels.  One statistics record
+// describes the whole run; there are no rounds.
+static int cluster_async(cc_graph* g, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
+                         int64_t* disagreements_out, cc_round_stats* stats, int32_t stats_cap, int32_t* stats_len) {
+  cudaStream_t s = g->stream;
+  int rc = ensure_objective_ws(g);
+  if (rc != CC_OK) return rc;
+  if (!g->async_grid) g->async_grid = async_grid_size(g->device);
+  RoundBuffers b;
+  rounds_carve(g->round_ws, g->n, g->max_deg, g->grid, &b);
+  b.n = g->n;
+  b.nnz = g->nnz;
+  b.max_deg = g->max_deg;
+  b.off = g->off;
+  b.col = g->col;
+  b.order = g->order;
+  b.nz_static = g->nz_row;
+  b.nz_n = g->nz_n;
+  const bool dev = is_device_ptr(labels_out);
+  int32_t* lab = labels_out;
+  if (!dev) {
+    if ((rc = ensure_labels_tmp(g)) != CC_OK) return rc;
+    lab = g->labels_tmp;
+  }
+  CC_TRY(cudaMemsetAsync(g->perm_err, 0, sizeof(int), s));
+  if (g->timing) CC_TRY(cudaEventRecord(g->ev[0], s));
+  CC_TRY(launch_permutation(g->n, seed, g->order, g->perm_ws, g->num_sms, g->perm_err, s));
+  if (g->timing) CC_TRY(cudaEventRecord(g->ev[1], s));
+  CC_TRY(launch_async_c4(b, g->async_grid, lab, s));
+  if (g->timing) CC_TRY(cudaEventRecord(g->ev[2], s));
+  CC_TRY(launch_disagreements(g->n, g->nnz, g->off, g->col, g->nz_row, g->nz_pos, g->nz_n, lab, g->obj_ws,
+                              g->obj_out, g->num_sms, s));
+  if (labels_out && !dev) CC_TRY(cudaMemcpyAsync(labels_out, lab, 4 * (size_t)g->n, cudaMemcpyDeviceToHost, s));
+  if (g->timing) CC_TRY(cudaEventRecord(g->ev[3], s));
+  CC_TRY(cudaMemcpyAsync(g->ctl_host, b.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  CC_TRY(cudaMemcpyAsync(g->obj_host, g->obj_out, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  int perr = 0;
+  CC_TRY(cudaMemcpyAsync(&perr, g->perm_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CC_TRY(cudaStreamSynchronize(s));
+  const Ctl& c = *g->ctl_host;
+  if (g->timing) {
+    for (int i = 0; i < 3; ++i) CC_TRY(cudaEventElapsedTime(&g->last_ms[i], g->ev[i], g->ev[i + 1]));
+    g->timed = true;
+  }
+  for (auto& x : g->last_phase_ns) x = 0;
+  g->phases_valid = true;
+  if (perr != 0) return status_of_device_err(perr);
+  if (c.err != 0) return status_of_device_err(c.err);
+  if (c.r_centers + c.r_noncenter != g->n || g->obj_host[2]) return CC_ERR_INTERNAL;
+  if (stats_cap > 0) {
+    cc_round_stats& r = stats[0];
+    r.n_alive = g->n;
+    r.delta = g->max_deg;
+    r.k = g->n;
+    r.centers = c.r_centers;
+    r.removed = g->n;
+    r.blocked = c.r_blocked;
+    r.edges = c.r_attached;
+    r.ns = 0;
+  }
+  if (stats_len) *stats_len = 1;
+  if (rounds_out) *rounds_out = 0;
+  if (disagreements_out) *disagreements_out = g->nnz / 2 - (int64_t)g->obj_host[0] + (int64_t)g->obj_host[1];
+  return CC_OK;
+}
+
 int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
                   int64_t* disagreements_out, cc_round_stats* stats, int32_t stats_cap, int32_t* stats_len) {
   if (!g) return CC_ERR_INVALID_ARG;
-  if (algo < CC_ALGO_C4 || algo > CC_ALGO_CLUSTERWILD_EST) return CC_ERR_INVALID_ARG;
+  if (algo < CC_ALGO_C4 || algo > CC_ALGO_C4_ASYNC) return CC_ERR_INVALID_ARG;
   if (stats_cap < 0 || (stats_cap > 0 && !stats)) return CC_ERR_INVALID_ARG;
   int64_t ppm = 0;
   int rc = eps_ppm_of(eps, &ppm);
@@ -365,6 +440,8 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
     CC_TRY(dalloc(&g->stats_dev, sizeof(RoundStat) * (size_t)stats_cap, s));
     g->stats_dev_cap = stats_cap;
   }
+  if (algo == CC_ALGO_C4_ASYNC)
+    return cluster_async(g, seed, labels_out, rounds_out, disagreements_out, stats, stats_cap, stats_len);
   RoundBuffers b;
   rounds_carve(g->round_ws, g->n, g->max_deg, g->grid, &b);
   b.n = g->n;
@@ -454,9 +531,8 @@ int cc_disagreements(cc_graph* g, const int32_t* labels, int64_t* out) {
   if (g->n == 0) { *out = 0; return CC_OK; }
   cudaSetDevice(g->device);
   cudaStream_t s = g->stream;
-  if (!g->obj_ws) CC_TRY(dalloc(&g->obj_ws, objective_workspace_bytes(g->n), s));
-  if (!g->obj_out) CC_TRY(dalloc(&g->obj_out, 4 * sizeof(unsigned long long), s));
-  if (!g->obj_host) CC_TRY(cudaMallocHost(&g->obj_host, 4 * sizeof(unsigned long long)));
+  int orc = ensure_objective_ws(g);
+  if (orc != CC_OK) return orc;
   const int32_t* lab = labels;
   if (!is_device_ptr(labels)) {
     int rc = ensure_labels_tmp(g);

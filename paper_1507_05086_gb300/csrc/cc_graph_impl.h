@@ -28,6 +28,7 @@ struct cc_graph {
   void* round_ws = nullptr;
   size_t round_ws_bytes = 0;
   int grid = 0;
+  int async_grid = 0;            // co-resident grid of the asynchronous C4 decisions
   int32_t* labels_tmp = nullptr;
   void* obj_ws = nullptr;
   unsigned long long* obj_out = nullptr;

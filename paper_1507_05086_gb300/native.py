@@ -20,8 +20,10 @@ C4 = 1
 CLUSTERWILD = 2
 C4_EST = 3              # the same with the practical schedule of Sec. 5
 CLUSTERWILD_EST = 4
+C4_ASYNC = 5            # C4 without rounds (Alg. 3); cluster() only
 ALGOS = {"c4": C4, "cw": CLUSTERWILD, "clusterwild": CLUSTERWILD, "c4-est": C4_EST, "cw-est": CLUSTERWILD_EST,
-         C4: C4, CLUSTERWILD: CLUSTERWILD, C4_EST: C4_EST, CLUSTERWILD_EST: CLUSTERWILD_EST}
+         "c4-async": C4_ASYNC,
+         C4: C4, CLUSTERWILD: CLUSTERWILD, C4_EST: C4_EST, CLUSTERWILD_EST: CLUSTERWILD_EST, C4_ASYNC: C4_ASYNC}
 
 CC_DEVICE_PTRS = 2
 CC_OFFSETS_I32 = 4

@@ -45,6 +45,14 @@ def test_binding_matches_header_stats_layout():
     assert tuple(fields) == native.ROUND_STAT_FIELDS
 
 
+def test_binding_matches_header_algorithm_ids():
+    from paper_1507_05086_gb300 import native
+    ids = dict((k, int(v)) for k, v in re.findall(r"#define\s+CC_ALGO_(\w+)\s+(\d+)", open(HEADER).read()))
+    assert ids == {"C4": native.C4, "CLUSTERWILD": native.CLUSTERWILD, "C4_EST": native.C4_EST,
+                   "CLUSTERWILD_EST": native.CLUSTERWILD_EST, "C4_ASYNC": native.C4_ASYNC}
+    assert native.ALGOS["c4-async"] == native.C4_ASYNC
+
+
 def test_product_and_oracle_are_independent():
     """The oracle never imports the CUDA package and the package never
     imports or links the oracle."""
