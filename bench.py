@@ -46,6 +46,7 @@ def parse_args(argv=None):
     p.add_argument("--batch-graphs", type=int, default=256,
                    help="Chung-Lu graphs in the batched-jobs measurement (0 = skip)")
     p.add_argument("--sec5", type=int, default=1, help="also time the Sec. 5 schedule once per algorithm (0 = skip)")
+    p.add_argument("--async-c4", type=int, default=1, help="also time C4 without rounds (Alg. 3) once (0 = skip)")
     p.add_argument("--serve-seconds", type=float, default=2.0,
                    help="length of the Poisson arrival stream for the serving measurement (0 = skip)")
     return p.parse_args(argv)
@@ -440,6 +441,21 @@ def run_ours(args):
             sec5[a + "-est"] = {"ms_per_clustering": pm + rm + lm, "rounds_kernel_ms": rm, "rounds": r,
                                 "disagreements": d, "edges_per_s": m / ((pm + rm + lm) / 1e3)}
 
+    # C4 without rounds (Alg. 3) on the same graph: same labels as C4 (and
+    # KwikCluster), one clustering after one warm-up; a comparison, not part
+    # of a step
+    async_c4 = None
+    if rank == 0 and args.async_c4 and "c4" in algos:
+        graph.cluster("c4-async", args.eps, 4244, labels_out=labels)
+        _, _, d, st = graph.cluster("c4-async", args.eps, 4245, labels_out=labels, stats_cap=1)
+        pm, km, om = graph.last_timings()
+        async_c4 = {"ms_per_clustering": pm + km + om, "permutation_ms": pm, "decide_push_ms": km,
+                    "labels_objective_ms": om, "disagreements": d, "blocked": int(st["blocked"][0]),
+                    "centers": int(st["centers"][0]), "edges_read": int(st["edges"][0]),
+                    "edges_per_s": m / ((pm + km + om) / 1e3),
+                    "what": "permutation; k_async_init, k_async_decide (one cooperative launch), "
+                            "k_async_push_long, k_async_labels; objective from the labels"}
+
     batch = serve = None
     if rank == 0 and (args.batch_graphs > 0 or args.serve_seconds > 0):
         bgs = batch_workload(max(args.batch_graphs, 64))
@@ -483,6 +499,7 @@ def run_ours(args):
             "batch": batch,
             "serve": serve,
             "sec5_schedule": sec5,
+            "async_c4": async_c4,
         }
         print(json.dumps(line), flush=True)
     graph.close()

@@ -12,7 +12,11 @@ quantities on the seeded synthetic graphs of ``graphgen`` through the C ABI:
   batched entry point (``cc_batch_jobs``), C4 and ClusterWild! on the same
   permutations (seed_j = base + j);
 * blocked counts come from the per-round statistics of ``cc_cluster_ex``
-  (C4 on the first ``--stats-perms`` permutations).
+  (C4 on the first ``--stats-perms`` permutations), and for C4 without rounds
+  (Alg. 3, ``CC_ALGO_C4_ASYNC``) from its one statistics record: the
+  vertices that waited on an undecided earlier neighbour.  The paper finds
+  fewer blocked vertices under the bulk-synchronous C4 than the asynchronous
+  one; its objective must equal C4's (both are KwikCluster).
 
 Prints one JSON object.  ``python quality.py --perms 100`` runs the paper's
 protocol on the small graphs; the defaults finish in about a minute.
@@ -58,11 +62,14 @@ def study(cc, g, eps: float, perms: int, stats_perms: int, seed: int):
         d4, r4 = cc.batch_jobs([graph], "c4", eps, seeds, perms)
         dw, rw = cc.batch_jobs([graph], "cw", eps, seeds, perms)
         d4, r4, dw, rw = (np.asarray(x).reshape(-1) for x in (d4, r4, dw, rw))
-        blocked = []
+        blocked, blocked_async = [], []
         for j in range(min(stats_perms, perms)):
             _, _, d, st = graph.cluster("c4", eps, seed + j, want_labels=False, stats_cap=1_000_000)
             assert d == d4[j]
             blocked.append(float(st["blocked"].sum()) / g.n)
+            _, _, da, sa = graph.cluster("c4-async", eps, seed + j, want_labels=False, stats_cap=1)
+            assert da == d4[j]
+            blocked_async.append(float(sa["blocked"][0]) / g.n)
     ratio = dw / np.maximum(d4, 1)
     return {
         "eps": eps,
@@ -74,6 +81,7 @@ def study(cc, g, eps: float, perms: int, stats_perms: int, seed: int):
         "cw_over_c4": summarize(ratio),
         "cw_worse_by_pct_mean": float((ratio.mean() - 1) * 100),
         "c4_blocked_pct_of_vertices": summarize(np.asarray(blocked) * 100) if blocked else None,
+        "c4_async_blocked_pct_of_vertices": summarize(np.asarray(blocked_async) * 100) if blocked_async else None,
     }
 
 

@@ -40,3 +40,7 @@ def test_quality_study_matches_oracle(cc, ora, gg):
     assert r["rounds_cw"]["max"] == max(rounds_cw)
     assert r["c4_blocked_pct_of_vertices"]["mean"] == pytest.approx(np.mean(blocked), rel=1e-12)
     assert r["cw_over_c4"]["mean"] == pytest.approx(np.mean(np.array(d_cw) / np.array(d_kc)), rel=1e-12)
+    # waits of C4 without rounds depend on the interleaving: only a range
+    # (its objective was checked against C4's inside the study)
+    a = r["c4_async_blocked_pct_of_vertices"]
+    assert 0.0 <= a["min"] <= a["max"] <= 100.0
