@@ -801,11 +801,14 @@ struct K {
       if (!want[q]) continue;
       const int32_t r = a[q].x, v = a[q].y;
       const uint32_t d = deg_of(ldcg(B.st + v));
-      set_rtag(B.rtag, v, (uint32_t)P().tag);
-      if (d == 0) {                             // no alive neighbour: singleton center
-        B.st[v] = kLab + (uint32_t)r;
+      if (d == 0) {
+        // no alive neighbour: a singleton center.  No pass can reach it
+        // again (its neighbours are all clustered, and later windows start
+        // past it), so it keeps its alive word and zero tag; the label pass
+        // reads an alive word of degree 0 as its own cluster.
         t.centers += 1;
       } else {
+        set_rtag(B.rtag, v, (uint32_t)P().tag);
         row[q] = __ldg(B.off + v);
         deg0[q] = __ldg(B.off + v + 1) - row[q];
         B.arank[v] = r;
@@ -1583,6 +1586,10 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
     int32_t* const lab = jobs[j].labels;
     for (int64_t v = (int64_t)k.bid * blockDim.x + threadIdx.x; v < rb.n; v += (int64_t)G * blockDim.x) {
       const uint32_t x = ldcg(rb.st + v);
+      if (x == kAlive) {                   // selected with residual degree 0: its own cluster
+        if (lab) lab[v] = (int32_t)v;
+        continue;
+      }
       const int64_t c = is_active(x) ? (int64_t)ldcg(rb.arank + v) : (int64_t)x - kLab;
       if (is_alive(x) || c < 0 || c >= rb.n) { k.fail(kErrInternal); continue; }
       const int32_t cv = ldcg(rb.order + c);
@@ -1638,6 +1645,10 @@ __global__ void k_finalize_labels(RoundBuffers B, int32_t* __restrict__ labels) 
   unsigned long long pairs = 0;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t x = B.st[v];
+    if (x == kAlive) {                     // selected with residual degree 0: its own cluster
+      if (labels) labels[v] = (int32_t)v;
+      continue;
+    }
     const int64_t c = is_active(x) ? (int64_t)B.arank[v] : (int64_t)x - kLab;   // last round's centers
     if (is_alive(x) || c < 0 || c >= n) {
       atomicCAS(&B.ctl->err, kOk, kErrInternal);

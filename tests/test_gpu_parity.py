@@ -322,6 +322,33 @@ def test_hubs_losing_degree_while_alive_match_oracle(cc, ora, gg):
                 assert d == ora.disagreements(g.off, g.col, olab)
 
 
+@pytest.mark.parametrize("name", ["rmat17", "chung_lu400k", "planted200k"])
+def test_larger_graphs_all_eps_match_oracle(cc, ora, gg, name):
+    """Graphs of 1.3e5-4e5 vertices, many of them selected with residual
+    degree 0 (singletons that keep their alive word): labels, rounds and
+    every round's statistics equal the oracle's, for both algorithms and
+    three eps, and for the Sec. 5 schedule."""
+    g = {"rmat17": lambda: gg.rmat(17, 16, seed=8),
+         "chung_lu400k": lambda: gg.chung_lu(400_000, 12.0, seed=4),
+         "planted200k": lambda: gg.planted_partition(n=200_000, q=300, seed=2, noise=300_000)}[name]()
+    with cc.Graph(g.off, g.col) as graph:
+        for algo, a in (("cw", 2), ("c4", 1)):
+            for eps, seed in ((0.1, 3), (0.5, 5), (0.9, 7)):
+                order = ora.permutation(g.n, seed)
+                olab, orr, _, ost = oracle_run(ora, g, order, a, eps)
+                lab, r, d, st = graph.cluster(algo, eps, seed, stats_cap=100_000)
+                assert np.array_equal(lab, olab) and r == orr, (algo, eps)
+                for f in STAT_FIELDS:
+                    assert np.array_equal(st[f], ost[f]), (algo, eps, f)
+                assert d == ora.disagreements(g.off, g.col, olab)
+        order = ora.permutation(g.n, 11)
+        olab, orr, _, ost = ora.rounds_bsp(g.off, g.col, order, 2, 0.5, 11, stats_cap=100_000)
+        lab, r, d, st = graph.cluster("cw-est", 0.5, 11, stats_cap=100_000)
+        assert np.array_equal(lab, olab) and r == orr
+        for f in STAT_FIELDS:
+            assert np.array_equal(st[f], ost[f]), f
+
+
 @pytest.mark.parametrize("algo,a", [("c4-est", 1), ("cw-est", 2)])
 @pytest.mark.parametrize("eps", [0.1, 0.5, 1.0])
 def test_sec5_schedule_matches_oracle(cc, ora, gg, algo, a, eps):
