@@ -410,6 +410,11 @@ def run_ours(args):
         off_h = torch.from_numpy(g.off).pin_memory()
         col_h = torch.from_numpy(g.col).pin_memory()
         lab_h = torch.empty(max(g.n, 1), dtype=torch.int32).pin_memory()
+        # one untimed step first: the library's memory pool grows to hold a
+        # second graph beside the resident one (a one-time mapping cost)
+        with cc.Graph(off_h.numpy(), col_h.numpy()) as gh:
+            for a, seed in zip(algos, step_seeds(rank, 9_999, len(algos))):
+                gh.cluster(a, args.eps, seed, labels_out=lab_h.numpy())
         torch.cuda.synchronize()
         es = torch.cuda.Event(enable_timing=True)
         ee = torch.cuda.Event(enable_timing=True)
@@ -426,7 +431,8 @@ def run_ours(args):
                "d2h_bytes_per_step": (4 * g.n + 16) * len(algos),
                "ms_per_step": e_ms / args.e2e_steps,
                "what": "per step: cc_graph_create from pinned host CSR (copy + validation), one C4 and one "
-                       "ClusterWild! cc_cluster with labels to pinned host memory, cc_graph_destroy"}
+                       "ClusterWild! cc_cluster with labels to pinned host memory, cc_graph_destroy; "
+                       "after one untimed step"}
 
     # the practical schedule of Sec. 5 (Delta-hat halving, binomial batches) on
     # the same graph, one clustering each: a comparison, not part of a step

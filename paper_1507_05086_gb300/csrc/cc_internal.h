@@ -38,7 +38,7 @@ struct Plan {
   int64_t k, need, win_lo, win_len;
   int64_t take, act_n, act_E, new_n;
   int64_t new_E, b_n, b_E, undecided;
-  int32_t th, r0, al_sel, al_ident;
+  int32_t th, r0, pad3, pad4;
   int32_t state, pad0, tag, pad2;      // tag: removal tag of the current round
 };
 static_assert(sizeof(Plan) == 128, "plan layout");
@@ -81,8 +81,6 @@ struct RoundBuffers {
   uint32_t* st;                // per-vertex state word
   uint32_t* rtag;              // per-vertex removal tag, 4 bits (8 vertices per word)
   int32_t* arank;              // rank of a vertex while it is active
-  int2* al0;                   // alive lists: (rank, vertex), rank-ordered
-  int2* al1;
   // row lists (see RowList in cc_device.cuh): vertex, first virtual edge,
   // CSR delta; actives also keep their rank, the blocked list stores the
   // active-list index in place of a vertex

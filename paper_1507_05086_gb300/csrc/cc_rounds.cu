@@ -36,8 +36,8 @@
 // degree in H is still >= tau it is the maximum over the whole graph;
 // otherwise a rebuild scans the compact list of alive non-isolated vertices,
 // takes the exact maximum D, sets tau = D/2 and refills H.  No work per
-// decrement.  The rank-ordered alive list used for selection is compacted
-// separately when most of its live range is dead.
+// decrement.  Selection scans pi itself from a cursor (entry i is the vertex
+// of rank i) and skips removed vertices by their tag.
 //
 // Every adjacency pass is edge-balanced (lbs_for_each), so hub rows of
 // power-law graphs are split across many warps.
@@ -53,7 +53,7 @@ constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanU = 4;                    // alive-list entries per thread per scan step
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
-constexpr int kRun = 0, kDone = 1, kRebuild = 2, kAbort = 3, kRebuildDelta = 4, kScanH = 5, kDrawBatch = 6;
+constexpr int kRun = 0, kDone = 1, kAbort = 3, kRebuildDelta = 4, kScanH = 5, kDrawBatch = 6;
 constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
 constexpr int64_t kInlineDecide = 4096;      // C4 blocked lists up to this size are decided by the coordinator
 
@@ -134,7 +134,7 @@ struct Coord {
   int64_t clusters;              // centers opened so far
   int64_t h_len, nz_len, nz_total;
   int32_t tau, delta, max_deg, d_new;
-  int algo, al_sel, al_ident, rebuilds_in_row;
+  int algo, rebuilds_in_row;
   int nz_sel, nz_static;
   int est;                       // the Sec. 5 schedule: Delta-hat and binomial batches
   int64_t period, rank_cursor;   // rounds per halving of Delta-hat; ranks of pi passed
@@ -304,12 +304,11 @@ struct K {
   __device__ LbsWarp* lbs_ws() const { return &S->u.w.lbs[threadIdx.x >> 5]; }
   __device__ AppendBuf* app_buf() const { return &S->u.w.app[threadIdx.x >> 5]; }
 
-  // Entry i of the current alive list: (rank, vertex).  Before the first
-  // compaction the list is implicit: entry i is (i, order[i]).
-  __device__ int2 al_at(int sel, int identity, int64_t i) const {
-    if (identity) return make_int2((int32_t)i, __ldg(B.order + i));
-    return ldcg((sel ? B.al1 : B.al0) + i);
-  }
+  // Entry i of the rank-ordered candidate list: (rank, vertex) = (i, pi(i)).
+  // Selection scans it from the cursor and skips removed vertices by their
+  // removal tag; the list is never compacted (every entry is scanned about
+  // once anyway, so a compaction pass would cost more than it saves).
+  __device__ int2 al_at(int64_t i) const { return make_int2((int32_t)i, __ldg(B.order + i)); }
 
   // contiguous slice of [lo, lo+len) for this block
   __device__ void slice(int64_t lo, int64_t len, int64_t* s, int64_t* e) const {
@@ -342,8 +341,6 @@ struct K {
       c.n_alive = B.n;
       c.cursor = 0;
       c.al_len = B.n;
-      c.al_ident = 1;
-      c.al_sel = 0;
       c.max_deg = B.max_deg;
       c.tau = 0x7FFFFFFF;         // empty heavy list: the first round rebuilds it
       c.h_len = 0;
@@ -407,8 +404,6 @@ struct K {
       p.th = 0;
       p.r0 = -1;
       p.tag = (int32_t)(c.round % kTagCycle) + 1;
-      p.al_sel = c.al_sel;
-      p.al_ident = c.al_ident;
     }
     __syncthreads();
   }
@@ -422,13 +417,7 @@ struct K {
     if (threadIdx.x == 0) {
       int dec = 1;
       if (c.n_alive <= 0) p.state = kDone;
-      else if (!c.al_ident && c.al_len - c.cursor > 4 * c.n_alive + 65536) {
-        p.state = kRebuild;               // compact the alive list first
-        p.al_sel = c.al_sel;
-        p.al_ident = c.al_ident;
-        p.win_lo = c.cursor;
-        p.win_len = c.al_len - c.cursor;
-      } else if (c.est) {
+      else if (c.est) {
         p.state = kDrawBatch;             // Sec. 5: draw the batch, no Delta
         const int64_t dh = sec5_delta_hat(c.max_deg, c.period, c.round);
         bool all;
@@ -438,8 +427,6 @@ struct K {
         p.need = (int64_t)thr;                                      // threshold bits
         p.take = all ? 1 : 0;
         p.k = (int64_t)perm_key(vload(&C->seed) ^ 0x5851F42D4C957F2Dull, (uint64_t)c.round);   // stream seed
-        p.al_sel = c.al_sel;
-        p.al_ident = c.al_ident;
       } else if (c.nz_len == 0) {
         dec = 2;                          // every alive vertex is isolated: Delta = 0
       } else if (c.h_len == 0 || c.h_len > kInlineH) {
@@ -550,27 +537,8 @@ struct K {
       const int64_t b = prefix_blocks();
       Coord& c = co();
       const int64_t end_rank = c.rank_cursor + b;
-      // first alive-list entry at or past end_rank (the list is rank-ordered)
-      int64_t end;
-      if (c.al_ident) {
-        end = end_rank < c.al_len ? end_rank : c.al_len;
-      } else {
-        int64_t lo = c.cursor, hi = c.al_len;
-        for (;;) {
-          const int64_t span = hi - lo;
-          if (span <= 0) break;
-          const int64_t step = (span + blockDim.x - 1) / blockDim.x;
-          const int64_t q = lo + (int64_t)threadIdx.x * step;
-          const bool below = q < hi && al_at(c.al_sel, 0, q).x < end_rank;
-          const int64_t f = __syncthreads_count(below);
-          if (step == 1) { lo += f; break; }
-          const int64_t nlo = f > 0 ? lo + (f - 1) * step + 1 : lo;
-          const int64_t nhi = lo + f * step < hi ? lo + f * step : hi;
-          lo = nlo;
-          hi = nhi;
-        }
-        end = lo;
-      }
+      // the list entry of rank end_rank ends the batch (entry i has rank i)
+      const int64_t end = end_rank < c.al_len ? end_rank : c.al_len;
       if (threadIdx.x == 0) {
         c.batch_end = end;
         c.rank_cursor = end_rank;
@@ -578,73 +546,6 @@ struct K {
       }
       __syncthreads();
       plan_selection(c.delta);
-    });
-  }
-
-  // ---------------- alive-list compaction -----------------------------------
-  __device__ bool rebuild() {
-    const int sel = P().al_sel, ident = P().al_ident;
-    const int64_t lo = P().win_lo, len = P().win_len;     // the live part of the list
-    int64_t s, e;
-    slice(lo, len, &s, &e);
-    int64_t cnt = 0;
-    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
-      int2 a[kScanU];
-#pragma unroll
-      for (int q = 0; q < kScanU; ++q) {
-        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
-        a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
-      }
-#pragma unroll
-      for (int q = 0; q < kScanU; ++q)
-        cnt += (a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0) ? 1 : 0;
-    }
-    cnt = block_sum<int64_t>(cnt, S->scr);
-    if (threadIdx.x == 0) B.blk_a[bid] = cnt;
-    if (!sync(0, [&] {
-          const int64_t tot = prefix_blocks();
-          if (threadIdx.x == 0) {
-            if (tot != co().n_alive) fail(kErrInternal);
-            S->plan.take = tot;
-          }
-        }))
-      return false;
-    // stable compaction into the other buffer
-    int2* dst = sel ? B.al0 : B.al1;
-    int64_t run = ldcg(B.blk_a + bid);
-    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
-      int2 a[kScanU];
-      bool alive[kScanU];
-      int64_t mine = 0;
-#pragma unroll
-      for (int q = 0; q < kScanU; ++q) {
-        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
-        a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
-      }
-#pragma unroll
-      for (int q = 0; q < kScanU; ++q) {
-        alive[q] = a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0;
-        mine += alive[q] ? 1 : 0;
-      }
-      int64_t tot;
-      int64_t o = run + block_exclusive_sum<int64_t>(mine, S->scr, &tot);
-#pragma unroll
-      for (int q = 0; q < kScanU; ++q)
-        if (alive[q]) dst[o++] = a[q];
-      run += tot;
-    }
-    return sync(1, [&] {
-      if (threadIdx.x == 0) {
-        Coord& c = co();
-        c.al_sel = sel ^ 1;
-        c.al_ident = 0;
-        c.al_len = S->plan.take;
-        c.cursor = 0;
-        c.rebuilds_in_row += 1;
-        if (c.rebuilds_in_row > 3) fail(kErrInternal);
-      }
-      __syncthreads();
-      co_decide_delta();
     });
   }
 
@@ -887,7 +788,6 @@ struct K {
 
   __device__ bool select(int algo) {
     for (;;) {
-      const int sel = P().al_sel, ident = P().al_ident;
       const int64_t wlo = P().win_lo, wlen = P().win_len;
       int64_t s, e;
       slice(wlo, wlen, &s, &e);
@@ -902,7 +802,7 @@ struct K {
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
         const int64_t i = s + (int64_t)threadIdx.x * kScanU + q;
-        a0[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
+        a0[q] = i < e ? al_at(i) : make_int2(0, -1);
       }
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
@@ -915,7 +815,7 @@ struct K {
 #pragma unroll
         for (int q = 0; q < 2 * kScanU; ++q) {
           const int64_t i = base + (int64_t)q * blockDim.x + threadIdx.x;
-          a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
+          a[q] = i < e ? al_at(i) : make_int2(0, -1);
         }
 #pragma unroll
         for (int q = 0; q < 2 * kScanU; ++q)
@@ -943,7 +843,7 @@ struct K {
 #pragma unroll
             for (int q = 0; q < kScanU; ++q) {
               const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
-              a[q] = i < e ? al_at(sel, ident, i) : make_int2(0, -1);
+              a[q] = i < e ? al_at(i) : make_int2(0, -1);
             }
 #pragma unroll
             for (int q = 0; q < kScanU; ++q) {
@@ -1294,10 +1194,6 @@ __device__ void run_job(K& k, int algo) {
 
   for (;;) {
     if (S.plan.state == kDone) break;
-    if (S.plan.state == kRebuild) {
-      if (!k.rebuild()) goto out;
-      continue;
-    }
     if (S.plan.state == kRebuildDelta) {
       if (!k.delta_rebuild()) goto out;
       continue;
@@ -1675,7 +1571,6 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   b += align_up(4 * nn);                 // st
   b += align_up(4 * ((nn >> 3) + 1));    // rtag
   b += align_up(4 * nn);                 // arank
-  b += 2 * align_up(8 * nn);             // al0, al1
   b += 2 * align_up(4 * nn) + 2 * align_up(8 * nn);   // act_v, act_r, act_e, act_d
   b += align_up(4 * nn) + 2 * align_up(8 * nn);       // new_v, new_e, new_d
   b += align_up(4 * nn);                 // size
@@ -1695,8 +1590,6 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   B->st = reinterpret_cast<uint32_t*>(take(4 * nn));
   B->rtag = reinterpret_cast<uint32_t*>(take(4 * ((nn >> 3) + 1)));
   B->arank = reinterpret_cast<int32_t*>(take(4 * nn));
-  B->al0 = reinterpret_cast<int2*>(take(8 * nn));
-  B->al1 = reinterpret_cast<int2*>(take(8 * nn));
   B->act_v = reinterpret_cast<int32_t*>(take(4 * nn));
   B->act_r = reinterpret_cast<int32_t*>(take(4 * nn));
   B->act_e = reinterpret_cast<int64_t*>(take(8 * nn));
