@@ -90,6 +90,7 @@ extern "C" {
 #define CC_ALGO_C4_ASYNC        5
 
 /* ---- cc_graph_create flags ----------------------------------------------- */
+#define CC_VALIDATE     1u   /* validate the CSR (always done; accepted for clarity) */
 #define CC_DEVICE_PTRS  2u   /* row_offsets/col_idx are device pointers, adopted by
                                 reference (caller keeps them alive until destroy) */
 #define CC_OFFSETS_I32  4u   /* row_offsets is int32[n+1] instead of int64[n+1]  */
@@ -119,7 +120,8 @@ typedef struct cc_round_stats {
  *   col_idx      int32[off[n]]: each row strictly increasing, no self loop,
  *                every entry in [0,n), and the graph symmetric (u in row v iff
  *                v in row u).  Isolated vertices are allowed.
- *   flags        CC_DEVICE_PTRS / CC_OFFSETS_I32.
+ *   flags        CC_VALIDATE / CC_DEVICE_PTRS / CC_OFFSETS_I32 (any other bit:
+ *                CC_ERR_INVALID_ARG).
  *   cuda_stream  cudaStream_t for all work on this graph (NULL = legacy stream).
  *   out          receives the handle.
  * Host arrays are copied; the caller may free them on return.  The CSR is

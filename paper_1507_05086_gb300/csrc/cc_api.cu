@@ -206,7 +206,7 @@ int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, 
   if (!out) return CC_ERR_INVALID_ARG;
   *out = nullptr;
   if (n < 0 || n > 2147483616LL || !row_offsets) return CC_ERR_INVALID_ARG;
-  if (flags & ~(CC_DEVICE_PTRS | CC_OFFSETS_I32)) return CC_ERR_INVALID_ARG;
+  if (flags & ~(CC_VALIDATE | CC_DEVICE_PTRS | CC_OFFSETS_I32)) return CC_ERR_INVALID_ARG;
   const bool dev = (flags & CC_DEVICE_PTRS) != 0, i32 = (flags & CC_OFFSETS_I32) != 0;
   cc_graph* g = new (std::nothrow) cc_graph();
   if (!g) return CC_ERR_OOM;

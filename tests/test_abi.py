@@ -37,6 +37,25 @@ def test_status_strings_without_gpu():
         assert lib.cc_status_string(code).decode() == text
 
 
+def test_graph_create_rejects_unknown_flags_without_gpu():
+    """Argument checks of cc_graph_create come before any device work: an
+    unknown flag bit (or a negative n) is CC_ERR_INVALID_ARG on any machine,
+    and CC_VALIDATE is a known bit."""
+    import ctypes
+    import numpy as np
+    from paper_1507_05086_gb300 import native
+    lib = native.load()
+    flags = dict((k, int(v, 16) if v.startswith("0x") else int(v))
+                 for k, v in re.findall(r"#define\s+CC_(VALIDATE|DEVICE_PTRS|OFFSETS_I32)\s+(\w+?)u", open(HEADER).read()))
+    assert flags == {"VALIDATE": 1, "DEVICE_PTRS": 2, "OFFSETS_I32": 4}
+    off = np.zeros(2, np.int64)
+    h = ctypes.c_void_p()
+    p = off.ctypes.data_as(ctypes.c_void_p)
+    assert lib.cc_graph_create(ctypes.c_int64(1), p, None, ctypes.c_uint32(8), None, ctypes.byref(h)) == -1
+    assert lib.cc_graph_create(ctypes.c_int64(-1), p, None, ctypes.c_uint32(1), None, ctypes.byref(h)) == -1
+    assert not h.value
+
+
 def test_binding_matches_header_stats_layout():
     from paper_1507_05086_gb300 import native
     text = open(HEADER).read()
