@@ -94,6 +94,8 @@ __device__ __forceinline__ bool kv_less(uint64_t ka, int32_t va, uint64_t kb, in
 // sort on the full (key, v).
 constexpr int kSubBits = 10;
 constexpr int kSub = 1 << kSubBits;
+// the sub-bucket counts are scanned two per thread
+static_assert(2 * kSortThreads >= kSub, "k_bucket_sort needs 2 * kSortThreads >= kSub");
 
 __global__ void __launch_bounds__(kSortThreads)
 k_bucket_sort(uint64_t seed, int bits, int64_t nb, const int64_t* __restrict__ start,
