@@ -218,9 +218,11 @@ int cc_last_timings(const cc_graph* g, float* ms_out);
 /*
  * Device-side breakdown of the last clustering's round kernel (always
  * recorded; globaltimer at every grid barrier).  ms_out[0..min(cap,7)) =
- * milliseconds spent in: alive-list rebuild (count), rebuild (compact and
- * refill), active-set count, active-set emit, centers + attachment, C4
- * fixpoint and blocked actives, removal and degree updates.
+ * milliseconds spent in: Delta from the heavy list (grid scans) and the
+ * count pass of its rebuild, the rebuild's compaction and refill, the Sec. 5
+ * batch draws, active-set selection, centers + attachment (C4: detection
+ * and classification too), C4 fixpoint and blocked actives, removal and
+ * degree updates.  (Zeros for CC_ALGO_C4_ASYNC.)
  */
 int cc_last_phase_times(const cc_graph* g, double* ms_out, int32_t cap);
 

@@ -66,9 +66,9 @@ struct Ctl {
   // results, written by the coordinator at the end
   int64_t round, n_alive;
   int done;
-  // time per phase category (ns): rebuild-count, rebuild-compact,
-  // select-count, select-emit, centers+attach, C4 fixpoint and blocked
-  // actives, removal+decrement, setup
+  // time per phase category (ns): Delta scan (heavy list, rebuild count),
+  // Delta rebuild (compaction, heavy refill), Sec. 5 draws, selection,
+  // centers+attach, C4 fixpoint and blocked actives, removal+decrement, setup
   unsigned long long ph_ns[8];
 };
 

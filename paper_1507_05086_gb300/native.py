@@ -227,7 +227,7 @@ class Graph:
         _check("cc_last_timings", self._lib.cc_last_timings(self._h, ctypes.cast(ms, ctypes.c_void_p)))
         return tuple(float(x) for x in ms)
 
-    PHASES = ("rebuild_count", "rebuild_compact", "select_count", "select_emit", "centers_attach",
+    PHASES = ("delta_scan", "delta_rebuild", "sec5_draws", "select", "centers_attach",
               "c4_fixpoint", "removal_decrement")
 
     def last_phase_times(self):
