@@ -227,6 +227,17 @@ int cc_last_timings(const cc_graph* g, float* ms_out);
 int cc_last_phase_times(const cc_graph* g, double* ms_out, int32_t cap);
 
 /*
+ * Test hook for the bounded waits (failure detection without a fault): the
+ * next cc_cluster / cc_cluster_ex call on g (CC_ALGO_C4 .. _EST) withholds the
+ * round kernel's barrier release after round `round` (0-based).  Every other
+ * block's wait on that release runs out after its 4 s bound, records
+ * CC_ERR_TIMEOUT and returns, so the call returns CC_ERR_TIMEOUT after about
+ * 4 s and the graph stays usable.  The hook applies to one call; a clustering
+ * with fewer rounds ends normally.  round < 0: CC_ERR_INVALID_ARG.
+ */
+int cc_debug_withhold_release(cc_graph* g, int32_t round);
+
+/*
  * cc_disagreements_static -- the same objective as cc_disagreements, for
  * callers that cannot allocate memory when they need it: code running inside
  * a fixed memory pool or arena, or under a "no allocation after start-up"

@@ -458,7 +458,9 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[0], s));
   CC_TRY(launch_permutation(g->n, seed, g->order, g->perm_ws, g->num_sms, g->perm_err, s));
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[1], s));
-  CC_TRY(launch_rounds(b, algo, ppm, seed, g->grid, s));
+  const int32_t withhold = g->withhold;
+  g->withhold = 0;                                  // the hook applies to one clustering
+  CC_TRY(launch_rounds(b, algo, ppm, seed, g->grid, s, withhold));
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[2], s));
   const bool dev = is_device_ptr(labels_out);
   if (labels_out && !dev) {
@@ -495,6 +497,12 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
     const int64_t m = g->nnz / 2;
     *disagreements_out = m - 2 * (int64_t)c.mc - (int64_t)c.mm + (int64_t)c.pairs;
   }
+  return CC_OK;
+}
+
+int cc_debug_withhold_release(cc_graph* g, int32_t round) {
+  if (!g || round < 0 || round > 2147483646) return CC_ERR_INVALID_ARG;
+  g->withhold = round + 1;
   return CC_OK;
 }
 

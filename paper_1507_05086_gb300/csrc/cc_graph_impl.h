@@ -29,6 +29,7 @@ struct cc_graph {
   size_t round_ws_bytes = 0;
   int grid = 0;
   int async_grid = 0;            // co-resident grid of the asynchronous C4 decisions
+  int32_t withhold = 0;          // test hook for the next clustering (cc_debug_withhold_release)
   int32_t* labels_tmp = nullptr;
   void* obj_ws = nullptr;
   unsigned long long* obj_out = nullptr;

@@ -52,6 +52,9 @@ struct Ctl {
   int algo;                       // 1 / 2: C4 / ClusterWild!; 3 / 4: the same with the Sec. 5 schedule
   int64_t eps_ppm;
   uint64_t seed;                  // seed of pi (the Sec. 5 batch draws derive from it)
+  // test hook: 1 + the round after which the coordinator withholds its
+  // release, so that every other block's bounded wait runs out (0: off)
+  int32_t withhold;
   alignas(16) Plan plan;
   // per-round counters, written by every block (lists pack items << 33 | edges)
   unsigned long long act_pack, new_pack, blk_pack;
@@ -148,7 +151,7 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
 // Largest co-resident grid for the persistent round kernel on this device.
 int rounds_grid_size(int device);
 cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, uint64_t seed, int grid,
-                          cudaStream_t stream);
+                          cudaStream_t stream, int32_t withhold = 0);
 // labels_out[v] = center vertex id (order[center rank]) when labels_out is
 // not null; always adds the pair term sum_c C(s_c, 2) to ctl->pairs.
 cudaError_t launch_finalize_labels(const RoundBuffers& b, int32_t* labels_out, cudaStream_t stream);

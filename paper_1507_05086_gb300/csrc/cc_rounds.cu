@@ -138,6 +138,7 @@ struct Coord {
   int nz_sel, nz_static;
   int est;                       // the Sec. 5 schedule: Delta-hat and binomial batches
   int64_t period, rank_cursor;   // rounds per halving of Delta-hat; ranks of pi passed
+  int32_t withhold;              // test hook (Ctl::withhold)
   int64_t batch_end;             // alive-list index that ends the round's batch
   unsigned long long t0, round_t0;
   unsigned long long ph_ns[8];
@@ -259,12 +260,20 @@ struct K {
       __syncthreads();
       // an error (here or in any block) travels in the plan as the abort state
       if (threadIdx.x == 0 && (!S->ok || ld_volatile_int(&C->err) != kOk)) S->plan.state = kAbort;
+      // test hook: after the chosen round the release is withheld; the other
+      // blocks' bounded waits run out (kErrTimeout) and every block unwinds
+      if (threadIdx.x == 0 && cat == 6 && S->co.withhold != 0 && S->co.round == S->co.withhold) {
+        S->plan.state = kAbort;
+        S->ok = 2;
+      }
       __syncthreads();
-      // publish: 128 bytes as eight 16-byte stores, then release
-      if (threadIdx.x < sizeof(Plan) / 16)
-        reinterpret_cast<int4*>(&C->plan)[threadIdx.x] = reinterpret_cast<const int4*>(&S->plan)[threadIdx.x];
-      __syncthreads();
-      if (threadIdx.x == 0) st_release(&C->gen, epoch);
+      if (S->ok != 2) {
+        // publish: 128 bytes as eight 16-byte stores, then release
+        if (threadIdx.x < sizeof(Plan) / 16)
+          reinterpret_cast<int4*>(&C->plan)[threadIdx.x] = reinterpret_cast<const int4*>(&S->plan)[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) st_release(&C->gen, epoch);
+      }
     } else {
       if (threadIdx.x == 0) {
         const uint64_t t0 = globaltimer_ns();
@@ -352,6 +361,7 @@ struct K {
       c.rebuilds_in_row = 0;
       c.algo = vload(&C->algo);
       c.eps_ppm = vload(&C->eps_ppm);
+      c.withhold = vload(&C->withhold);
       c.est = c.algo >= 3;                // the Sec. 5 schedule
       if (c.est) c.algo -= 2;
       c.period = c.est ? sec5_period(c.n, c.max_deg, c.eps_ppm) : 0;
@@ -1511,7 +1521,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
   }
 }
 
-__global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm, uint64_t seed) {
+__global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm, uint64_t seed, int32_t withhold) {
   const int64_t n = B.n;
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = __ldg(B.off + v + 1) - __ldg(B.off + v);
@@ -1527,6 +1537,7 @@ __global__ void k_init_state(RoundBuffers B, int algo, int64_t eps_ppm, uint64_t
     C->algo = algo;
     C->eps_ppm = eps_ppm;
     C->seed = seed;
+    C->withhold = withhold;
     C->n_alive = n;
     C->done = n > 0 ? 0 : 1;
   }
@@ -1624,10 +1635,10 @@ int rounds_grid_size(int device) {
 }
 
 cudaError_t launch_rounds(const RoundBuffers& b, int algo, int64_t eps_ppm, uint64_t seed, int grid,
-                          cudaStream_t stream) {
+                          cudaStream_t stream, int32_t withhold) {
   cudaError_t e = cudaMemsetAsync(b.ctl, 0, sizeof(Ctl), stream);
   if (e != cudaSuccess) return e;
-  k_init_state<<<grid, 256, 0, stream>>>(b, algo, eps_ppm, seed);
+  k_init_state<<<grid, 256, 0, stream>>>(b, algo, eps_ppm, seed, withhold);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (b.n <= 0) return cudaSuccess;

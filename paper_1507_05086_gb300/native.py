@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True):
         lib.cc_last_timings.argtypes = [vp, vp]
         lib.cc_last_phase_times.restype = ci
         lib.cc_last_phase_times.argtypes = [vp, vp, i32]
+        lib.cc_debug_withhold_release.restype = ci
+        lib.cc_debug_withhold_release.argtypes = [vp, i32]
         lib.cc_disagreements_static.restype = ci
         lib.cc_disagreements_static.argtypes = [i64, vp, vp, vp, vp, vp]
         lib.cc_batch_jobs.restype = ci
@@ -229,6 +231,12 @@ class Graph:
 
     PHASES = ("delta_scan", "delta_rebuild", "sec5_draws", "select", "centers_attach",
               "c4_fixpoint", "removal_decrement")
+
+    def debug_withhold_release(self, round_: int):
+        """Test hook: the next clustering withholds its barrier release after
+        round `round_`; the other blocks' bounded waits run out and the call
+        raises CCError with CC_ERR_TIMEOUT."""
+        _check("cc_debug_withhold_release", self._lib.cc_debug_withhold_release(self._h, int(round_)))
 
     def last_phase_times(self):
         """Milliseconds per phase of the last clustering's round kernel."""
