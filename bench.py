@@ -346,10 +346,10 @@ def run_ours(args):
     algos = args.algos.split(",")
     g = load_graph(args.workload)
     m = g.m
-    # end to end through the public API with host buffers, measured before
-    # the device-resident graph below exists (with that graph and its
-    # workspace still allocated the same steps were measured 30-40 % slower;
-    # the cause was not identified)
+    # end to end through the public API with host buffers, measured first
+    # (run after the device-resident steps and the random-read ceiling below,
+    # the same steps were measured 30-40 % slower; a second resident graph
+    # alone does not slow them, and the cause was not identified)
     e2e = None
     if args.e2e_steps > 0:
         off_h = torch.from_numpy(g.off).pin_memory()
