@@ -151,20 +151,27 @@ def measured_hbm_peak():
 # DRAM traffic of the round kernel per algorithmic byte, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum of one launch on R-MAT scale 24,
 # ClusterWild!, eps 0.5: 5.991 GB against 4.497 GB algorithmic), keyed by a
-# digest of the kernel's sources: a changed kernel reports traffic null until
-# it is captured again.  Traffic grows with the scanned entries and vertices,
+# digest of the kernel's code (comments and blank lines left out): a changed
+# kernel reports traffic null until it is captured again.  Traffic grows with the scanned entries and vertices,
 # so the ratio scales the capture to the timed workload.
 ROUNDS_SOURCES = ("paper_1507_05086_gb300/csrc/cc_rounds.cu", "paper_1507_05086_gb300/csrc/cc_device.cuh",
                   "paper_1507_05086_gb300/csrc/cc_internal.h")
-ROUNDS_TRAFFIC_PER_BYTE = {"47fcd4a54c059bf7": 5.990908e9 / 4.497261200e9}
+ROUNDS_TRAFFIC_PER_BYTE = {"ad6899ca79fc6d64": 5.990908e9 / 4.497261200e9}
 
 
 def rounds_sources_digest() -> str:
+    """Digest of the round kernel's code: its sources without comments and
+    blank lines (a comment edit leaves the compiled kernel unchanged)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ROUNDS_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f), encoding="utf-8") as fh:
+            text = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        for line in text.splitlines():
+            code = line.split("//", 1)[0].rstrip()
+            if code:
+                h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
