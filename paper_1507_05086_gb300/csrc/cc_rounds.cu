@@ -30,14 +30,17 @@
 // eighth of the state words' footprint, so the random reads of the edge
 // passes and of the selection scans mostly hit L2.  A tag equal to the
 // current round's only says "maybe removed this round" (a vertex removed
-// 15, 30, ... rounds earlier carries it too); the state word decides.  Delta_i (max residual degree, exact
-// every round) comes from a heavy list H: every alive vertex whose degree was
-// >= tau when H was built.  Degrees only fall, so if the largest current
-// degree in H is still >= tau it is the maximum over the whole graph;
-// otherwise a rebuild scans the compact list of alive non-isolated vertices,
-// takes the exact maximum D, sets tau = D/2 and refills H.  No work per
-// decrement.  Selection scans pi itself from a cursor (entry i is the vertex
-// of rank i) and skips removed vertices by their tag.
+// 15, 30, ... rounds earlier carries it too); the state word decides.
+//
+// Delta_i (max residual degree, exact every round) comes from a heavy list H:
+// every alive vertex whose degree was >= tau when H was built.  Degrees only
+// fall, so if the largest current degree in H is still >= tau it is the
+// maximum over the whole graph; otherwise a rebuild scans the compact list of
+// alive non-isolated vertices, takes the exact maximum D, sets tau = D/2 and
+// refills H.  No work per decrement.  Selection scans pi itself from a cursor
+// (entry i is the vertex of rank i) and skips removed vertices by their tag;
+// a selected vertex of residual degree 0 is a singleton center for which
+// nothing is written (the label pass reads its alive word of degree 0).
 //
 // Every adjacency pass is edge-balanced (lbs_for_each), so hub rows of
 // power-law graphs are split across many warps.
@@ -51,7 +54,7 @@ namespace {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kScanU = 4;                    // alive-list entries per thread per scan step
+constexpr int kScanU = 4;                    // list entries per thread per scan step
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
 constexpr int kRun = 0, kDone = 1, kAbort = 3, kRebuildDelta = 4, kScanH = 5, kDrawBatch = 6;
 constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
@@ -139,7 +142,7 @@ struct Coord {
   int est;                       // the Sec. 5 schedule: Delta-hat and binomial batches
   int64_t period, rank_cursor;   // rounds per halving of Delta-hat; ranks of pi passed
   int32_t withhold;              // test hook (Ctl::withhold)
-  int64_t batch_end;             // alive-list index that ends the round's batch
+  int64_t batch_end;             // rank (index in pi) that ends the round's batch
   unsigned long long t0, round_t0;
   unsigned long long ph_ns[8];
 };
@@ -418,7 +421,7 @@ struct K {
     __syncthreads();
   }
 
-  // Coordinator, at a round boundary: finish, compact the alive list, or get
+  // Coordinator, at a round boundary: finish, draw the Sec. 5 batch, or get
   // Delta from the heavy list (inline when short, else by a grid scan), or
   // rebuild the heavy list.
   __device__ void co_decide_delta() {
@@ -529,8 +532,8 @@ struct K {
   // Every block counts its share of the round's draws below the threshold
   // (plan: win_len trials, need = threshold bits, take = every trial
   // succeeds, k = stream seed); the coordinator adds them up, moves the rank
-  // cursor past the batch, finds where the batch ends in the alive list and
-  // plans the round's single selection window.
+  // cursor past the batch and plans the round's single selection window, the
+  // batch's ranks of pi.
   __device__ bool draw_batch() {
     const int64_t trials = P().win_len;
     const uint64_t thr = (uint64_t)P().need, s = (uint64_t)P().k;
