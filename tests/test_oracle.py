@@ -235,6 +235,24 @@ def test_rounds_with_singleton_batches_equal_kwikcluster(ora, gg):
                 assert np.all((st["k"] == 1) | (st["delta"] == 0))
 
 
+@pytest.mark.parametrize("eps", [0.1, 0.5, 0.9])
+def test_round_count_within_the_analysis_bound(ora, gg, eps):
+    """Sec. 4 bounds the rounds by O((1/eps) log n log Delta) with high
+    probability; on graphs of 1e4-6e4 vertices the oracle's count stays under
+    2 (1/eps) ln(n) log2(Delta) (a loose constant: informational, not the
+    paper's)."""
+    import math
+    for g in (gg.erdos_renyi(10_000, 20 / 9_999, seed=0), gg.rmat(15, 16, seed=2),
+              gg.planted_partition(n=60_000, q=200, seed=1, noise=60_000)):
+        delta = int(np.diff(g.off).max())
+        bound = 2.0 / eps * math.log(g.n) * math.log2(max(delta, 2))
+        for seed in (0, 1):
+            order = ora.permutation(g.n, seed)
+            for algo in (ora.ALGO_C4, ora.ALGO_CW):
+                _, r, _, _ = ora.rounds(g.off, g.col, order, algo, eps, 1)
+                assert 1 <= r <= bound, (g.n, eps, seed, algo, r, bound)
+
+
 def test_delta_scan_equals_degree_table(ora, gg):
     for g in _graphs(gg, 14):
         order = ora.permutation(g.n, 4)
