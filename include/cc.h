@@ -232,8 +232,9 @@ int cc_last_phase_times(const cc_graph* g, double* ms_out, int32_t cap);
  * round kernel's barrier release after round `round` (0-based).  Every other
  * block's wait on that release runs out after its 4 s bound, records
  * CC_ERR_TIMEOUT and returns, so the call returns CC_ERR_TIMEOUT after about
- * 4 s and the graph stays usable.  The hook applies to one call; a clustering
- * with fewer rounds ends normally.  round < 0: CC_ERR_INVALID_ARG.
+ * 4 s and the graph stays usable.  The hook applies to the next clustering
+ * call only (a CC_ALGO_C4_ASYNC call consumes it without effect); a
+ * clustering with fewer rounds ends normally.  round < 0: CC_ERR_INVALID_ARG.
  */
 int cc_debug_withhold_release(cc_graph* g, int32_t round);
 

@@ -357,6 +357,7 @@ int cc_permutation(cc_graph* g, uint64_t seed, int32_t* order_out) {
 static int cluster_async(cc_graph* g, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
                          int64_t* disagreements_out, cc_round_stats* stats, int32_t stats_cap, int32_t* stats_len) {
   cudaStream_t s = g->stream;
+  g->withhold = 0;                                  // the round kernel's test hook has no effect here
   int rc = ensure_objective_ws(g);
   if (rc != CC_OK) return rc;
   if (!g->async_grid) g->async_grid = async_grid_size(g->device);
