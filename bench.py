@@ -43,6 +43,10 @@ def parse_args(argv=None):
     p.add_argument("--algos", default="cw,c4")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--configs", type=int, default=1,
+                   help="also time the other workload configurations once each (0 = skip)")
+    p.add_argument("--parity", type=int, default=1,
+                   help="check the last timed step's labels against the oracle on the full graph (CPU leg)")
     p.add_argument("--batch-graphs", type=int, default=256,
                    help="Chung-Lu graphs in the batched-jobs measurement (0 = skip)")
     p.add_argument("--sec5", type=int, default=1, help="also time the Sec. 5 schedule once per algorithm (0 = skip)")
@@ -149,14 +153,15 @@ def measured_hbm_peak():
 
 
 # DRAM traffic of the round kernel per algorithmic byte, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of one launch on R-MAT scale 24,
-# ClusterWild!, eps 0.5: 5.991 GB against 4.497 GB algorithmic), keyed by a
-# digest of the kernel's code (comments and blank lines left out): a changed
-# kernel reports traffic null until it is captured again.  Traffic grows with the scanned entries and vertices,
-# so the ratio scales the capture to the timed workload.
+# (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass metric set, of the
+# second k_rounds launch of a run on the default workload, R-MAT scale 26,
+# eps 0.5: ClusterWild! 53.13 GB against 18.19 GB algorithmic, C4 53.32 GB
+# against 18.80 GB), keyed by a digest of the kernel's code (comments and
+# blank lines left out): a changed kernel reports traffic null until it is
+# captured again.
 ROUNDS_SOURCES = ("paper_1507_05086_gb300/csrc/cc_rounds.cu", "paper_1507_05086_gb300/csrc/cc_device.cuh",
                   "paper_1507_05086_gb300/csrc/cc_internal.h")
-ROUNDS_TRAFFIC_PER_BYTE = {"ad6899ca79fc6d64": 5.990908e9 / 4.497261200e9}
+ROUNDS_TRAFFIC_PER_BYTE = {"ad6899ca79fc6d64": (53.13e9 + 53.32e9) / (18.19e9 + 18.80e9)}
 
 
 def rounds_sources_digest() -> str:
@@ -205,6 +210,63 @@ def rounds_algorithmic_bytes(edges_scanned: int, n: int) -> int:
     word; every vertex costs its two row offsets (16), its own state read and
     write (8) and its alive-list entry (8)."""
     return 8 * edges_scanned + 32 * n
+
+
+def host_cpu():
+    """Core count and CPU model of the host the oracle runs on."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"host_cores": os.cpu_count(), "cpu_model": model, "machine": platform.machine()}
+
+
+def oracle_parity(g, checks, eps):
+    """The oracle on the full workload for the last timed step's permutations:
+    C4 against serial KwikCluster (Alg. 1; C4 returns exactly its clustering),
+    ClusterWild! against the oracle's literal rounds (Alg. 2).  checks: algo ->
+    (seed, labels, rounds, D) of the GPU.  Each check runs serially on its own
+    host core; the two run side by side."""
+    import concurrent.futures
+
+    import numpy as np
+
+    import oracle
+    oracle.build()
+
+    def one(a):
+        seed, lab, r, d = checks[a]
+        t0 = time.perf_counter()
+        order = oracle.permutation(g.n, seed)
+        if a == "c4":
+            olab = oracle.kwik(g.off, g.col, order)
+            orr = None
+        else:
+            olab, orr, _, _ = oracle.rounds(g.off, g.col, order, 2, eps)
+        dt = time.perf_counter() - t0
+        od = oracle.disagreements(g.off, g.col, olab)
+        ok = bool(np.array_equal(lab, olab)) and od == d and (orr is None or orr == r)
+        return a, {"seed": seed, "labels_equal": bool(np.array_equal(lab, olab)), "disagreements_equal": od == d,
+                   "rounds_equal": None if orr is None else orr == r, "ok": ok, "oracle_s": dt,
+                   "oracle": "KwikCluster (Alg. 1)" if a == "c4" else "literal Alg. 2 rounds"}
+
+    with concurrent.futures.ThreadPoolExecutor(len(checks)) as ex:
+        return dict(ex.map(one, list(checks)))
 
 
 def cpu_sample_run(algos, eps, seed_base=7):
@@ -311,6 +373,71 @@ def measure_serving(cc, torch, gs, seconds: float, rate: float = 2000.0, eps: fl
             x.close()
 
 
+def _time_clusterings(graph, algo, eps, seeds, labels):
+    """Device time (permutation + rounds + labels, CUDA events) of one
+    clustering per seed after one warm-up; returns the means and the last
+    run's statistics."""
+    graph.cluster(algo, eps, 99, labels_out=labels)
+    ms, rk, rs, ds, st = [], [], [], [], None
+    for s in seeds:
+        _, r, d, st = graph.cluster(algo, eps, s, labels_out=labels, stats_cap=100_000)
+        pm, rm, lm = graph.last_timings()
+        ms.append(pm + rm + lm)
+        rk.append(rm)
+        rs.append(r)
+        ds.append(d)
+    return statistics.mean(ms), statistics.mean(rk), rs, ds, st
+
+
+def per_round_bandwidth(st, peak):
+    """Algorithmic GB/s of every round of the round kernel (8 B per scanned
+    adjacency entry, 32 B per vertex removed in the round, over the round's
+    device time): median, 10th and 90th percentiles, and the byte-weighted
+    mean (total bytes over total time)."""
+    import numpy as np
+    b = 8.0 * st["edges"] + 32.0 * st["removed"]
+    t = np.maximum(st["ns"], 1) / 1e9
+    gbs = b / t / 1e9
+    return {"rounds": int(b.size), "median_gbs": float(np.median(gbs)), "p10_gbs": float(np.percentile(gbs, 10)),
+            "p90_gbs": float(np.percentile(gbs, 90)), "weighted_gbs": float(b.sum() / t.sum() / 1e9),
+            "weighted_frac": float(b.sum() / t.sum() / 1e9 / peak)}
+
+
+def measure_configs(cc, torch, graph26, labels26, peak):
+    """The other workload configurations, each timed on its own (not part of
+    a step): ClusterWild! at eps 0.1 and 0.9 on R-MAT scale 26; R-MAT scale 24
+    with per-round bandwidth; the planted-partition graph at three eps."""
+    import graphgen
+    out = {}
+    for eps in (0.1, 0.9):
+        ms, rk, rs, ds, st = _time_clusterings(graph26, "cw", eps, (5001, 5002), labels26)
+        out[f"rmat26_cw_eps{eps}"] = {"ms_per_clustering": ms, "rounds_kernel_ms": rk, "rounds": rs,
+                                      "disagreements": ds, "edges_per_s": graph26.m / (ms / 1e3)}
+    g = graphgen.workload("rmat24")
+    with cc.Graph(g.off, g.col) as gr:
+        gr.set_timing(True)
+        lab = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        for a in ("cw", "c4"):
+            ms, rk, rs, ds, st = _time_clusterings(gr, a, 0.5, (6001, 6002), lab)
+            out[f"rmat24_{a}_eps0.5"] = {"ms_per_clustering": ms, "rounds_kernel_ms": rk, "rounds": rs,
+                                         "disagreements": ds, "edges_per_s": gr.m / (ms / 1e3),
+                                         "per_round": per_round_bandwidth(st, peak)}
+        del lab
+    del g
+    g = graphgen.workload("planted1m")
+    with cc.Graph(g.off, g.col) as gr:
+        gr.set_timing(True)
+        lab = torch.empty(g.n, dtype=torch.int32, device="cuda")
+        planted = gr.disagreements(g.aux)
+        for a in ("cw", "c4"):
+            for eps in (0.1, 0.5, 0.9):
+                ms, rk, rs, ds, st = _time_clusterings(gr, a, eps, (7001, 7002), lab)
+                out[f"planted1m_{a}_eps{eps}"] = {"ms_per_clustering": ms, "rounds": rs, "disagreements": ds,
+                                                   "planted_labels_disagreements": planted,
+                                                   "edges_per_s": gr.m / (ms / 1e3)}
+    return out
+
+
 def run_reference(args):
     rank, _, world = dist_env()
     if world > 1 and rank != 0:
@@ -389,11 +516,14 @@ def run_ours(args):
 
     graph = cc.Graph(g.off, g.col)
     graph.set_timing(True)
-    labels = torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda")
+    # one label buffer per algorithm, so that the last timed step's labels of
+    # both can be checked against the oracle after the timed region
+    labels_of = {a: torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda") for a in algos}
+    labels = labels_of[algos[0]]
 
     for s in range(args.warmup):
         for a, seed in zip(algos, step_seeds(rank, -1 - s, len(algos))):
-            graph.cluster(a, args.eps, seed, labels_out=labels)
+            graph.cluster(a, args.eps, seed, labels_out=labels_of[a])
 
     def barrier():
         if world > 1:
@@ -410,7 +540,7 @@ def run_ours(args):
         start.record()
         for s in range(args.steps):
             for a, seed in zip(algos, step_seeds(rank, s, len(algos))):
-                _, r, d, st = graph.cluster(a, args.eps, seed, labels_out=labels, stats_cap=100_000)
+                _, r, d, st = graph.cluster(a, args.eps, seed, labels_out=labels_of[a], stats_cap=100_000)
                 pm, rm, lm = graph.last_timings()
                 per[a]["ms"].append(pm + rm + lm)
                 per[a]["perm_ms"].append(pm)
@@ -423,6 +553,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
     elapsed = start.elapsed_time(end)
+    # the last timed step's outputs, for the oracle check of the CPU leg
+    last_step = {a: (seed, labels_of[a][:g.n].cpu().numpy(), per[a]["rounds"][-1], per[a]["D"][-1])
+                 for a, seed in zip(algos, step_seeds(rank, args.steps - 1, len(algos)))}
     clusterings = args.steps * len(algos)
     edges_done = m * clusterings
     value, tmax = reduce_across_ranks(elapsed, edges_done, world, torch.device("cuda", local_rank))
@@ -473,6 +606,10 @@ def run_ours(args):
                     "what": "permutation; k_async_init, k_async_decide (one cooperative launch), "
                             "k_async_push_long, k_async_labels; objective from the labels"}
 
+    configs = None
+    if rank == 0 and args.configs:
+        configs = measure_configs(cc, torch, graph, labels, peak)
+
     batch = serve = None
     if rank == 0 and (args.batch_graphs > 0 or args.serve_seconds > 0):
         bgs = batch_workload(max(args.batch_graphs, 64))
@@ -481,13 +618,17 @@ def run_ours(args):
         if args.serve_seconds > 0:
             serve = measure_serving(cc, torch, bgs[:64], args.serve_seconds)
 
-    cpu = None
+    cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         e, dt = cpu_sample_run(algos, args.eps)
         cpu = {"value": e / dt, "unit": "edges/s", "cores": 1, "kind": "oracle",
                "sample": f"serial C oracle (permutation + Alg. 2 rounds, C4 and ClusterWild!, eps={args.eps}) "
                          f"on R-MAT scale {SAMPLE_SCALE} from the same generator, {e // len(algos)} edges, "
-                         f"{dt:.1f} s"}
+                         f"{dt:.1f} s",
+               **host_cpu()}
+        # the timed step's output on the full workload against the oracle
+        if args.parity:
+            parity = oracle_parity(g, last_step, args.eps)
 
     if rank == 0:
         line = {
@@ -513,6 +654,8 @@ def run_ours(args):
             "roofline": roofline,
             "random_access": random_access,
             "cpu_baseline": cpu,
+            "parity": parity,
+            "configs": configs,
             "batch": batch,
             "serve": serve,
             "sec5_schedule": sec5,

@@ -233,8 +233,10 @@ int cc_last_phase_times(const cc_graph* g, double* ms_out, int32_t cap);
  * block's wait on that release runs out after its 4 s bound, records
  * CC_ERR_TIMEOUT and returns, so the call returns CC_ERR_TIMEOUT after about
  * 4 s and the graph stays usable.  The hook applies to the next clustering
- * call only (a CC_ALGO_C4_ASYNC call consumes it without effect); a
- * clustering with fewer rounds ends normally.  round < 0: CC_ERR_INVALID_ARG.
+ * call on g only, whatever that call's outcome: a call that fails its
+ * argument checks, runs on an empty graph, fails to allocate or uses
+ * CC_ALGO_C4_ASYNC consumes it without effect; a clustering with fewer
+ * rounds ends normally.  round < 0: CC_ERR_INVALID_ARG.
  */
 int cc_debug_withhold_release(cc_graph* g, int32_t round);
 
@@ -242,10 +244,13 @@ int cc_debug_withhold_release(cc_graph* g, int32_t round);
  * cc_disagreements_static -- the same objective as cc_disagreements, for
  * callers that cannot allocate memory when they need it: code running inside
  * a fixed memory pool or arena, or under a "no allocation after start-up"
- * rule.  It allocates nothing: besides the caller's buffers it uses one
- * scratch area compiled into the library (about 4 MB per GPU, reserved when
- * the library is loaded on that GPU and held until the process exits).  The
- * paper has no counterpart; this is a deployment variant.
+ * rule.  Besides the caller's buffers it uses one scratch area compiled into
+ * the library (about 4 MB per GPU, held until the process exits).  Under
+ * CUDA's lazy module loading (the default) that area is mapped on a device
+ * by the first call there, which may therefore make the driver allocate and
+ * can return CC_ERR_OOM on a full GPU: make one call per device at start-up,
+ * before any no-allocation phase or stream capture.  Later calls allocate
+ * nothing.  The paper has no counterpart; this is a deployment variant.
  *   n            number of vertices, 0 <= n <= CC_STATIC_MAX_N (larger n:
  *                CC_ERR_INVALID_ARG).
  *   row_offsets  device int64[n+1], col_idx device int32[off[n]]: a CSR as
@@ -253,10 +258,9 @@ int cc_debug_withhold_release(cc_graph* g, int32_t round);
  *   labels       device int32[n], values in [0, n).
  *   out          device int64: receives D, or -1 if a label is out of range.
  *   cuda_stream  stream for the work; the call returns without waiting.
- * Every call shares the one scratch area: calls whose work overlaps on the GPU
- * race and must be ordered by the caller.  The first call on a device looks
- * up the scratch address (cudaGetSymbolAddress); make it before any stream
- * capture starts.
+ * Every call shares the one scratch area (cleared by each call): calls whose
+ * work overlaps on the GPU race and must be ordered by the caller.  The
+ * first call on a device looks up the scratch address (cudaGetSymbolAddress).
  */
 #define CC_STATIC_MAX_N (1 << 20)
 int cc_disagreements_static(int64_t n, const int64_t* row_offsets, const int32_t* col_idx,

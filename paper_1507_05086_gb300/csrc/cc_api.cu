@@ -357,7 +357,6 @@ int cc_permutation(cc_graph* g, uint64_t seed, int32_t* order_out) {
 static int cluster_async(cc_graph* g, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
                          int64_t* disagreements_out, cc_round_stats* stats, int32_t stats_cap, int32_t* stats_len) {
   cudaStream_t s = g->stream;
-  g->withhold = 0;                                  // the round kernel's test hook has no effect here
   int rc = ensure_objective_ws(g);
   if (rc != CC_OK) return rc;
   if (!g->async_grid) g->async_grid = async_grid_size(g->device);
@@ -422,6 +421,10 @@ static int cluster_async(cc_graph* g, uint64_t seed, int32_t* labels_out, int32_
 int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
                   int64_t* disagreements_out, cc_round_stats* stats, int32_t stats_cap, int32_t* stats_len) {
   if (!g) return CC_ERR_INVALID_ARG;
+  // the test hook belongs to this call whatever its outcome (a bad argument,
+  // an empty graph, a failed allocation, the asynchronous algorithm)
+  const int32_t withhold = g->withhold;
+  g->withhold = 0;
   if (algo < CC_ALGO_C4 || algo > CC_ALGO_C4_ASYNC) return CC_ERR_INVALID_ARG;
   if (stats_cap < 0 || (stats_cap > 0 && !stats)) return CC_ERR_INVALID_ARG;
   int64_t ppm = 0;
@@ -459,8 +462,6 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[0], s));
   CC_TRY(launch_permutation(g->n, seed, g->order, g->perm_ws, g->num_sms, g->perm_err, s));
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[1], s));
-  const int32_t withhold = g->withhold;
-  g->withhold = 0;                                  // the hook applies to one clustering
   CC_TRY(launch_rounds(b, algo, ppm, seed, g->grid, s, withhold));
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[2], s));
   const bool dev = is_device_ptr(labels_out);

@@ -7,14 +7,20 @@
 // loops, real-time paths), or callers that must not touch the allocator
 // while other work is in flight.  This entry point works only on buffers the
 // caller already owns plus one fixed scratch area that is part of the
-// library's image: a file-scope __device__ array reserved when the library is
-// loaded on a GPU and kept until the process exits.
+// library's image: a file-scope __device__ array that, once mapped on a GPU,
+// stays there until the process exits.
+//
+// With CUDA's lazy module loading (the default) the array is mapped when this
+// file's module is first used on a device, which is the first call of this
+// entry point there (its cudaGetSymbolAddress lookup).  That first call may
+// therefore make the driver allocate device memory, and it can fail with
+// CC_ERR_OOM on a full GPU: make one call at start-up on each device, before
+// any no-allocation phase or stream capture begins.  Later calls allocate
+// nothing.
 //
 // The scratch is shared by every call on that device, so calls whose work
 // overlaps on the GPU race with each other and must be serialised by the
-// caller (one stream, or events).  The first call on a device looks up the
-// device address of the scratch with cudaGetSymbolAddress; make that first
-// call before any stream capture begins.
+// caller (one stream, or events).
 #include <cstdint>
 #include <mutex>
 
@@ -48,16 +54,45 @@ __global__ void k_static_sizes(int64_t n, const int32_t* __restrict__ labels, in
   }
 }
 
-// One warp per row: entries (u, w) of the CSR with label[u] == label[w].
+// Entries (u, w) of the CSR with label[u] == label[w].  One warp per row;
+// a row longer than kStaticLongRow (a hub of a power-law graph) is queued in
+// shared memory and read by the whole block once the block's warps are done
+// with their short rows, so that one hub does not hold a single warp for the
+// whole kernel (a full queue sends the row back to its warp).
+constexpr int kStaticLongRow = 2048;
+constexpr int kStaticLongCap = 64;
+
 __global__ void k_static_intra(int64_t n, const int64_t* __restrict__ off, const int32_t* __restrict__ col,
                                const int32_t* __restrict__ labels, unsigned long long* acc) {
+  __shared__ int32_t longq[kStaticLongCap];
+  __shared__ int nlong;
   const int lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) nlong = 0;
+  __syncthreads();
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   unsigned long long cnt = 0;
   for (int64_t u = gw; u < n; u += nw) {
+    const int64_t e0 = off[u], e1 = off[u + 1];
+    if (e1 - e0 > kStaticLongRow) {
+      int slot = 0;
+      if (lane == 0) slot = atomicAdd(&nlong, 1);
+      slot = __shfl_sync(ccg::FULL, slot, 0);
+      if (slot < kStaticLongCap) {
+        if (lane == 0) longq[slot] = (int32_t)u;
+        continue;
+      }
+    }
     const int32_t lu = labels[u];
-    for (int64_t e = off[u] + lane; e < off[u + 1]; e += 32) cnt += labels[col[e]] == lu ? 1 : 0;
+    for (int64_t e = e0 + lane; e < e1; e += 32) cnt += labels[col[e]] == lu ? 1 : 0;
+  }
+  __syncthreads();
+  const int nq = nlong < kStaticLongCap ? nlong : kStaticLongCap;
+  for (int q = 0; q < nq; ++q) {
+    const int32_t u = longq[q];
+    const int32_t lu = labels[u];
+    const int64_t e1 = off[u + 1];
+    for (int64_t e = off[u] + threadIdx.x; e < e1; e += blockDim.x) cnt += labels[col[e]] == lu ? 1 : 0;
   }
   cnt = ccg::warp_sum(cnt);
   if (lane == 0 && cnt) atomicAdd(acc, cnt);
@@ -86,10 +121,17 @@ int scratch_for_device(int dev, StaticScratch* out) {
   if (dev < 0 || dev >= kMaxDevices) return CC_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_mu);
   if (!g_dev[dev].size) {
+    // Under lazy module loading (the CUDA default) this lookup is what loads
+    // the module, and with it maps the scratch array on this device: a lack
+    // of memory shows up here, and is reported as such.
     void* ps = nullptr;
     void* pa = nullptr;
-    if (cudaGetSymbolAddress(&ps, g_static_size) != cudaSuccess) return CC_ERR_CUDA;
-    if (cudaGetSymbolAddress(&pa, g_static_acc) != cudaSuccess) return CC_ERR_CUDA;
+    cudaError_t e = cudaGetSymbolAddress(&ps, g_static_size);
+    if (e == cudaSuccess) e = cudaGetSymbolAddress(&pa, g_static_acc);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA;
+    }
     g_dev[dev].size = static_cast<int32_t*>(ps);
     g_dev[dev].acc = static_cast<unsigned long long*>(pa);
   }

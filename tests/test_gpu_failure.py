@@ -44,3 +44,19 @@ def test_withheld_release_times_out_and_the_graph_stays_usable(cc, ora, gg):
         assert np.array_equal(lab, olab) and r == orr
         with pytest.raises(cc.CCError):
             graph.debug_withhold_release(-1)
+        # a call that fails its argument checks consumes the hook too
+        graph.debug_withhold_release(1)
+        with pytest.raises(cc.CCError) as ei:
+            graph.cluster("cw", 1.5, 7)
+        assert ei.value.status == -1
+        lab, r, d = graph.cluster("cw", 0.5, 7)
+        assert np.array_equal(lab, olab) and r == orr
+
+
+def test_asynchronous_call_consumes_the_hook(cc, gg):
+    g = gg.rmat(10, 8, seed=1)
+    with cc.Graph(g.off, g.col) as graph:
+        graph.debug_withhold_release(0)
+        graph.cluster("c4-async", 0.5, 1)            # consumes the hook without effect
+        lab, r, d = graph.cluster("cw", 0.5, 1)      # runs to the end
+        assert r > 0

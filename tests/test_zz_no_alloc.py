@@ -61,6 +61,38 @@ def test_static_matches_allocating_entry_on_two_calls(env):
         assert _static(lib, torch, g.n, off_d, col_d, lab_d, out_d) == d_cw
 
 
+def test_static_matches_oracle_on_power_law_hubs_and_recovers_from_a_bad_label(env, ora):
+    """R-MAT with 2^20 vertices (the scratch's limit; hub rows far longer
+    than one warp's share): the count equals the oracle's.  A labelling with
+    one value out of range gives -1; the next valid call is exact again (the
+    flag in the shared scratch is cleared).  n = 0 gives 0."""
+    torch, graphgen, cc, lib = env
+    g = graphgen.rmat(20, 16, seed=5)
+    assert g.n == 1 << 20 and int(np.diff(g.off).max()) > 10_000
+    off_d = torch.from_numpy(g.off).cuda()
+    col_d = torch.from_numpy(g.col).cuda()
+    out_d = torch.zeros(1, dtype=torch.int64, device="cuda")
+    order = ora.permutation(g.n, 4)
+    kc = ora.kwik(g.off, g.col, order)
+    for lab in (kc, (np.arange(g.n) // 7).astype(np.int32)):
+        lab_d = torch.from_numpy(np.ascontiguousarray(lab, np.int32)).cuda()
+        assert _static(lib, torch, g.n, off_d, col_d, lab_d, out_d) == ora.disagreements(g.off, g.col, lab)
+    bad = kc.copy()
+    bad[12345] = g.n
+    lab_d = torch.from_numpy(bad).cuda()
+    assert _static(lib, torch, g.n, off_d, col_d, lab_d, out_d) == -1
+    lab_d = torch.from_numpy(kc).cuda()
+    assert _static(lib, torch, g.n, off_d, col_d, lab_d, out_d) == ora.disagreements(g.off, g.col, kc)
+    off0 = torch.zeros(1, dtype=torch.int64, device="cuda")
+    out_d.fill_(77)
+    stream = torch.cuda.current_stream().cuda_stream
+    rc = lib.cc_disagreements_static(0, ctypes.c_void_p(off0.data_ptr()), None, None,
+                                     ctypes.c_void_p(out_d.data_ptr()), ctypes.c_void_p(stream))
+    assert rc == 0
+    torch.cuda.synchronize()
+    assert int(out_d.item()) == 0
+
+
 def test_static_rejects_sizes_above_its_scratch(env):
     torch, graphgen, cc, lib = env
     out_d = torch.zeros(1, dtype=torch.int64, device="cuda")
