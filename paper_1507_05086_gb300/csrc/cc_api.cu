@@ -184,6 +184,8 @@ int cc_graph_destroy(cc_graph* g) {
   if (g->own_col) dfree(g->col, s);
   dfree(g->nz_row, s);
   dfree(g->nz_pos, s);
+  dfree(g->dsort, s);
+  dfree(g->dge, s);
   dfree(g->perm_ws, s);
   dfree(g->order, s);
   dfree(g->round_ws, s);
@@ -296,6 +298,19 @@ int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, 
     launch_nonempty_rows(n, g->off, g->nz_row, g->nz_pos, nws, nz_dev, g->num_sms, s);
     cudaMemcpyAsync(&g->nz_n, nz_dev, 8, cudaMemcpyDeviceToHost, s);
     if ((rc = from_cuda(cudaStreamSynchronize(s))) != CC_OK) { dfree(vws, s); dfree(nws, s); break; }
+    // the non-isolated vertices by degree (for the round kernel's Delta)
+    {
+      void* dws = nullptr;
+      if ((rc = from_cuda(dalloc(&g->dsort, 4 * (size_t)(g->nz_n > 0 ? g->nz_n : 1), s))) != CC_OK ||
+          (rc = from_cuda(dalloc(&g->dge, 8 * ((size_t)g->max_deg + 2), s))) != CC_OK ||
+          (rc = from_cuda(dalloc(&dws, degree_order_workspace_bytes(g->max_deg), s))) != CC_OK) {
+        dfree(dws, s); dfree(vws, s); dfree(nws, s);
+        break;
+      }
+      rc = from_cuda(launch_degree_order(g->nz_n, g->nz_row, g->off, g->max_deg, g->dsort, g->dge, dws, g->num_sms, s));
+      dfree(dws, s);
+      if (rc != CC_OK) { dfree(vws, s); dfree(nws, s); break; }
+    }
     for (int c = 0; c < chunks; ++c) {
       if (g->col_ready[c]) cudaStreamWaitEvent(s, g->col_ready[c], 0);
       launch_validate_edges(n, cut[c], cut[c + 1], c == chunks - 1, g->nz_row, g->nz_pos, g->nz_n, g->col, vws,
@@ -370,6 +385,8 @@ static int cluster_async(cc_graph* g, uint64_t seed, int32_t* labels_out, int32_
   b.order = g->order;
   b.nz_static = g->nz_row;
   b.nz_n = g->nz_n;
+  b.dsort = g->dsort;
+  b.dge = g->dge;
   const bool dev = is_device_ptr(labels_out);
   int32_t* lab = labels_out;
   if (!dev) {
@@ -456,6 +473,8 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
   b.order = g->order;
   b.nz_static = g->nz_row;
   b.nz_n = g->nz_n;
+  b.dsort = g->dsort;
+  b.dge = g->dge;
   b.stats = g->stats_dev;
   b.stats_cap = stats_cap;
   CC_TRY(cudaMemsetAsync(g->perm_err, 0, sizeof(int), s));
@@ -588,6 +607,7 @@ int run_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, con
       const cc_graph* g = gs[i];
       jb = BatchJob{};
       jb.off = g->off; jb.col = g->col; jb.nz = g->nz_row; jb.nz_n = g->nz_n;
+      jb.dsort = g->dsort; jb.dge = g->dge;
       jb.n = g->n; jb.nnz = g->nnz; jb.max_deg = g->max_deg;
       jb.seed = seeds[i] + (uint64_t)j;
       jb.err = 1;

@@ -21,6 +21,9 @@ struct cc_graph {
   int32_t* nz_row = nullptr;
   int64_t* nz_pos = nullptr;
   int64_t nz_n = 0;
+  // non-isolated vertices by degree, largest first, and counts of degree >= t
+  int32_t* dsort = nullptr;
+  int64_t* dge = nullptr;
   // cached workspaces (grown on demand)
   void* perm_ws = nullptr;
   size_t perm_ws_bytes = 0;

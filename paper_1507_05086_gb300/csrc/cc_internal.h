@@ -100,6 +100,11 @@ struct RoundBuffers {
   int32_t* nz1;
   const int32_t* nz_static;    // the graph's non-isolated vertices
   int64_t nz_n;
+  // the graph's non-isolated vertices by degree, largest first, and the
+  // number of vertices of degree >= t for t = 0 .. max_deg + 1 (the Delta
+  // rebuild reads the prefix that can still hold the maximum)
+  const int32_t* dsort;
+  const int64_t* dge;
   uint8_t* blk_flag;
   uint8_t* hit_c;
   uint8_t* hit_p;
@@ -125,6 +130,8 @@ struct BatchJob {
   const int32_t* col;
   const int32_t* nz;
   int64_t nz_n;
+  const int32_t* dsort;
+  const int64_t* dge;
   int64_t n, nnz;
   int32_t max_deg;
   int32_t err;          // result: device status (0 = ok, 1 = not run)
@@ -176,6 +183,12 @@ cudaError_t launch_validate_edges(int64_t n, int64_t e0, int64_t e1, bool last, 
                                   const int64_t* nz_pos, int64_t nz_n, const int32_t* col, void* ws, int num_sms,
                                   cudaStream_t stream);
 cudaError_t launch_offsets_i32_to_i64(int64_t n, const int32_t* in, int64_t* out, cudaStream_t stream);
+// dsort (int32[nz_n]): the non-isolated vertices, largest degree first;
+// dge (int64[max_deg + 2]): dge[t] = number of vertices of degree >= t.
+// ws: degree_order_workspace_bytes(max_deg), free once the work is done.
+size_t degree_order_workspace_bytes(int32_t max_deg);
+cudaError_t launch_degree_order(int64_t nz_n, const int32_t* nz_row, const int64_t* off, int32_t max_deg,
+                                int32_t* dsort, int64_t* dge, void* ws, int num_sms, cudaStream_t stream);
 size_t nonempty_workspace_bytes(int64_t n);
 cudaError_t launch_nonempty_rows(int64_t n, const int64_t* off, int32_t* nz_row, int64_t* nz_pos, void* ws,
                                  int64_t* count_dev, int num_sms, cudaStream_t stream);

@@ -181,7 +181,102 @@ __global__ void k_nz_write(int64_t n, const int64_t* __restrict__ off, const int
   }
 }
 
+// ---- the non-isolated vertices ordered by degree --------------------------
+// dsort lists the non-isolated vertices, largest degree first (ties in any
+// order), and dge[t] (t = 0 .. max_deg + 1) counts the vertices of degree
+// >= t, so dsort[0 .. dge[t]) are exactly the vertices of degree >= t.  The
+// round kernel's Delta rebuild reads such a prefix.  Degrees below kDegSmall
+// are counted and placed through shared-memory bins (one global atomic per
+// block and bin), larger ones (few vertices) directly.
+constexpr int kDegSmall = 2048;
+constexpr int kDegThreads = 1024;
+constexpr int kDegPer = 4;
+
+__global__ void __launch_bounds__(kDegThreads) k_deg_hist(int64_t nz_n, const int32_t* __restrict__ nz_row,
+                                                         const int64_t* __restrict__ off,
+                                                         unsigned long long* __restrict__ cnt) {
+  __shared__ int bin[kDegSmall];
+  for (int b = threadIdx.x; b < kDegSmall; b += blockDim.x) bin[b] = 0;
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nz_n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = nz_row[i];
+    const int64_t d = off[v + 1] - off[v];
+    if (d < kDegSmall) atomicAdd(&bin[d], 1);
+    else atomicAdd(cnt + d, 1ull);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < kDegSmall; b += blockDim.x)
+    if (bin[b]) atomicAdd(cnt + b, (unsigned long long)bin[b]);
+}
+
+// One block: dge[t] = sum of cnt[d] over d >= t (suffix sums, top down), then
+// cnt[d] becomes the first position of degree d in dsort, dge[d + 1].
+__global__ void __launch_bounds__(kDegThreads) k_deg_suffix(int64_t max_deg, unsigned long long* __restrict__ cnt,
+                                                           int64_t* __restrict__ dge) {
+  __shared__ int64_t scr[33];
+  const int64_t len = max_deg + 2;              // indices 0 .. max_deg + 1
+  int64_t run = 0;
+  for (int64_t base = 0; base < len; base += blockDim.x) {
+    const int64_t idx = len - 1 - (base + threadIdx.x);
+    const int64_t x = idx >= 0 ? (int64_t)cnt[idx] : 0;
+    int64_t tot;
+    const int64_t ex = block_exclusive_sum<int64_t>(x, scr, &tot);
+    if (idx >= 0) dge[idx] = run + ex + x;
+    run += tot;
+  }
+  __syncthreads();
+  for (int64_t d = threadIdx.x; d <= max_deg; d += blockDim.x) cnt[d] = (unsigned long long)dge[d + 1];
+}
+
+__global__ void __launch_bounds__(kDegThreads) k_deg_scatter(int64_t nz_n, const int32_t* __restrict__ nz_row,
+                                                            const int64_t* __restrict__ off,
+                                                            unsigned long long* __restrict__ cur,
+                                                            int32_t* __restrict__ dsort) {
+  __shared__ int bin[kDegSmall];
+  __shared__ unsigned long long base[kDegSmall];
+  const int64_t tile = (int64_t)kDegThreads * kDegPer;
+  for (int64_t t0 = blockIdx.x * tile; t0 < nz_n; t0 += (int64_t)gridDim.x * tile) {
+    for (int b = threadIdx.x; b < kDegSmall; b += blockDim.x) bin[b] = 0;
+    __syncthreads();
+    int32_t v[kDegPer];
+    int32_t d[kDegPer];
+    int r[kDegPer];
+#pragma unroll
+    for (int q = 0; q < kDegPer; ++q) {
+      const int64_t i = t0 + (int64_t)q * blockDim.x + threadIdx.x;
+      v[q] = i < nz_n ? nz_row[i] : -1;
+      d[q] = v[q] >= 0 ? (int32_t)(off[v[q] + 1] - off[v[q]]) : 0;
+      r[q] = 0;
+      if (v[q] < 0) continue;
+      if (d[q] < kDegSmall) r[q] = atomicAdd(&bin[d[q]], 1);
+      else dsort[atomicAdd(cur + d[q], 1ull)] = v[q];
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kDegSmall; b += blockDim.x)
+      if (bin[b]) base[b] = atomicAdd(cur + b, (unsigned long long)bin[b]);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kDegPer; ++q)
+      if (v[q] >= 0 && d[q] < kDegSmall) dsort[base[d[q]] + r[q]] = v[q];
+    __syncthreads();
+  }
+}
+
 }  // namespace
+
+size_t degree_order_workspace_bytes(int32_t max_deg) { return align_up(8 * ((size_t)max_deg + 2)); }
+
+cudaError_t launch_degree_order(int64_t nz_n, const int32_t* nz_row, const int64_t* off, int32_t max_deg,
+                                int32_t* dsort, int64_t* dge, void* ws, int num_sms, cudaStream_t stream) {
+  unsigned long long* cnt = static_cast<unsigned long long*>(ws);
+  cudaError_t e = cudaMemsetAsync(cnt, 0, degree_order_workspace_bytes(max_deg), stream);
+  if (e != cudaSuccess) return e;
+  const int g = num_sms > 0 ? num_sms : 1;
+  if (nz_n > 0) k_deg_hist<<<g, kDegThreads, 0, stream>>>(nz_n, nz_row, off, cnt);
+  k_deg_suffix<<<1, kDegThreads, 0, stream>>>(max_deg, cnt, dge);
+  if (nz_n > 0) k_deg_scatter<<<g, kDegThreads, 0, stream>>>(nz_n, nz_row, off, cnt, dsort);
+  return cudaGetLastError();
+}
 
 size_t objective_workspace_bytes(int64_t n) {
   return align_up(4 * (size_t)(n > 0 ? n : 1)) + align_up(8 * 4);

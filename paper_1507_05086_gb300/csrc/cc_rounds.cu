@@ -57,8 +57,10 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kScanU = 4;                    // list entries per thread per scan step
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
 constexpr int kRun = 0, kDone = 1, kAbort = 3, kRebuildDelta = 4, kScanH = 5, kDrawBatch = 6;
+constexpr int kRebuildDeg = 7, kRebuildHeavy = 8;   // Delta search over the degree order, heavy refill
 constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
 constexpr int64_t kInlineDecide = 4096;      // C4 blocked lists up to this size are decided by the coordinator
+constexpr int64_t kInlineRebuild = 8192;     // heavy-list rebuilds over prefixes up to this size run in the coordinator
 
 // State word of a vertex (uint32):
 //   alive ........... kAlive | residual degree
@@ -135,10 +137,14 @@ struct Coord {
   int64_t n, n_alive, cursor, al_len, k, round, stats_cap, eps_ppm;
   int64_t need, win_lo, win_len, r_edges, fix_iter;
   int64_t clusters;              // centers opened so far
-  int64_t h_len, nz_len, nz_total;
+  int64_t h_len;                 // heavy list length
+  int64_t nz_len, nz_total;      // compact list of alive non-isolated vertices
+  int64_t rb_lo, rb_hi;          // degree-order search: next segment of the prefix
+  int32_t rb_t, rb_D;            // every vertex of full degree >= rb_t read; largest current degree seen
   int32_t tau, delta, max_deg, d_new;
   int algo, rebuilds_in_row;
   int nz_sel, nz_static;
+  int delta_zero;                // a rebuild found no alive vertex with an alive neighbour
   int est;                       // the Sec. 5 schedule: Delta-hat and binomial batches
   int64_t period, rank_cursor;   // rounds per halving of Delta-hat; ranks of pi passed
   int32_t withhold;              // test hook (Ctl::withhold)
@@ -359,6 +365,7 @@ struct K {
       c.nz_len = B.nz_n;          // non-isolated vertices, from the graph
       c.nz_static = 1;
       c.nz_sel = 0;
+      c.delta_zero = 0;
       c.round = 0;
       c.clusters = 0;
       c.rebuilds_in_row = 0;
@@ -424,7 +431,7 @@ struct K {
   // Coordinator, at a round boundary: finish, draw the Sec. 5 batch, or get
   // Delta from the heavy list (inline when short, else by a grid scan), or
   // rebuild the heavy list.
-  __device__ void co_decide_delta() {
+  __device__ __noinline__ void co_decide_delta() {
     Coord& c = co();
     Plan& p = S->plan;
     if (threadIdx.x == 0) {
@@ -440,11 +447,12 @@ struct K {
         p.need = (int64_t)thr;                                      // threshold bits
         p.take = all ? 1 : 0;
         p.k = (int64_t)perm_key(vload(&C->seed) ^ 0x5851F42D4C957F2Dull, (uint64_t)c.round);   // stream seed
-      } else if (c.nz_len == 0) {
+      } else if (c.delta_zero) {
         dec = 2;                          // every alive vertex is isolated: Delta = 0
-      } else if (c.h_len == 0 || c.h_len > kInlineH) {
-        if (c.h_len == 0) { p.state = kRebuildDelta; set_nz_plan(); }
-        else { p.state = kScanH; p.win_lo = 0; p.win_len = c.h_len; }
+      } else if (c.h_len == 0) {
+        dec = 3;                          // no heavy list yet: build it
+      } else if (c.h_len > kInlineH) {
+        p.state = kScanH; p.win_lo = 0; p.win_len = c.h_len;
       } else {
         dec = 0;                          // scan the short heavy list here
       }
@@ -452,6 +460,12 @@ struct K {
     }
     __syncthreads();
     if (S->dec == 2) { plan_selection(0); return; }
+    if (S->dec == 3) {
+      // before the first round every vertex is alive with its full degree:
+      // the search starts at the largest degree, which it finds at once
+      start_rebuild(co().round == 0 ? co().max_deg : 1);
+      return;
+    }
     if (S->dec) return;
     // the whole block reads the heavy list, eight entries per thread at a time
     // so that the dependent loads overlap
@@ -480,15 +494,149 @@ struct K {
     if (threadIdx.x == 0) S->dec = mx >= co().tau ? 1 : 0;
     __syncthreads();
     if (S->dec) { plan_selection(mx); return; }
-    if (threadIdx.x == 0) { S->plan.state = kRebuildDelta; set_nz_plan(); }
+    // The new maximum D lies in [max(mx, 0), tau): every vertex outside the
+    // heavy list had a degree below tau when the list was built.
+    start_rebuild(co().tau >= 2 ? co().tau >> 1 : 1);
+  }
+
+  // ---------------- Delta rebuild: where to look -------------------------------
+  // A rebuild needs the exact maximum D over the alive vertices and a new heavy
+  // list holding every alive vertex of degree >= max(1, D/2).  Degrees only
+  // fall, so a vertex of current degree >= x has full degree >= x.  The search
+  // reads the degree order (dsort, largest full degree first) in segments:
+  // after every vertex of full degree >= t has been read, the largest current
+  // degree seen is D exactly if it is >= t (no unread vertex can reach t);
+  // otherwise t halves and the next segment is read.  The heavy list then
+  // comes from the prefix of full degree >= D/2.  Segments up to
+  // kInlineRebuild vertices are read by the coordinator block inside the
+  // barrier; longer ones by the grid.  Once the prefix to read exceeds a
+  // quarter of the compact list of alive non-isolated vertices (vertex order,
+  // dead vertices dropped at each of its rebuilds), that list is cheaper and
+  // the rebuild switches to it.
+  __device__ __noinline__ void start_rebuild(int32_t t0) {
+    if (threadIdx.x == 0) {
+      Coord& c = co();
+      const int32_t hi = c.max_deg + 1;
+      c.rb_t = t0 < 1 ? 1 : (t0 > hi ? hi : t0);
+      c.rb_lo = 0;
+      c.rb_hi = __ldg(B.dge + c.rb_t);
+      c.rb_D = 0;
+      c.rebuilds_in_row += 1;
+      if (c.rebuilds_in_row > 2) fail(kErrInternal);
+    }
     __syncthreads();
+    rebuild_advance();
+  }
+
+  // Coordinator block: read segments inline until D is known (then refill the
+  // heavy list, inline or by planning a grid pass), or plan a grid step.
+  __device__ __noinline__ void rebuild_advance() {
+    for (;;) {
+      if (threadIdx.x == 0) {
+        Coord& c = co();
+        Plan& p = S->plan;
+        const int64_t limit = c.nz_len / 4;
+        const int64_t seg = c.rb_hi - c.rb_lo;
+        int dec;
+        if (seg > 0) {
+          dec = seg <= kInlineRebuild ? 0 : (c.rb_hi > limit ? 4 : 1);
+        } else if (c.rb_D >= c.rb_t || c.rb_t <= 1) {
+          if (c.rb_D <= 0) {
+            dec = 5;                                  // nothing alive has an alive neighbour
+          } else {
+            c.tau = c.rb_D >= 2 ? c.rb_D >> 1 : 1;
+            c.rb_hi = __ldg(B.dge + c.tau);           // heavy candidates: full degree >= tau
+            dec = c.rb_hi <= kInlineRebuild ? 2 : (c.rb_hi > limit ? 4 : 3);
+          }
+        } else {
+          c.rb_t = c.rb_t >= 2 ? c.rb_t >> 1 : 1;
+          c.rb_hi = __ldg(B.dge + c.rb_t);
+          dec = -1;
+        }
+        if (dec == 1) { p.state = kRebuildDeg; p.win_lo = c.rb_lo; p.win_len = seg; }
+        if (dec == 3) { p.state = kRebuildHeavy; p.win_lo = 0; p.win_len = c.rb_hi; p.th = c.tau; C->h_pack = 0; }
+        if (dec == 4) { p.state = kRebuildDelta; set_nz_plan(); }
+        S->dec = dec;
+      }
+      __syncthreads();
+      const int dec = S->dec;
+      __syncthreads();
+      if (dec == -1) continue;
+      if (dec == 0) {                                 // read a short segment here
+        const int64_t m = deg_max_over(co().rb_lo, co().rb_hi);
+        if (threadIdx.x == 0) {
+          Coord& c = co();
+          c.rb_D = m > c.rb_D ? (int32_t)m : c.rb_D;
+          c.rb_lo = c.rb_hi;
+        }
+        __syncthreads();
+        continue;
+      }
+      if (dec == 2) {                                 // refill a short heavy list here
+        const int32_t tau = co().tau;
+        const int64_t len = co().rb_hi;
+        if (threadIdx.x == 0) S->bcast[0] = 0;
+        __syncthreads();
+        for (int64_t base = threadIdx.x; base < len; base += (int64_t)kScanU * blockDim.x) {
+          int32_t v[kScanU];
+          uint32_t x[kScanU];
+#pragma unroll
+          for (int q = 0; q < kScanU; ++q) {
+            const int64_t i = base + (int64_t)q * blockDim.x;
+            v[q] = i < len ? __ldg(B.dsort + i) : -1;
+          }
+#pragma unroll
+          for (int q = 0; q < kScanU; ++q) x[q] = v[q] >= 0 ? ldcg(B.st + v[q]) : 0u;
+#pragma unroll
+          for (int q = 0; q < kScanU; ++q)
+            if (is_alive(x[q]) && deg_of(x[q]) > 0 && (int64_t)deg_of(x[q]) >= tau)
+              B.hv[atomicAdd(reinterpret_cast<unsigned long long*>(&S->bcast[0]), 1ull)] = v[q];
+        }
+        __syncthreads();
+        finish_rebuild(co().rb_D, S->bcast[0]);
+        return;
+      }
+      if (dec == 5) { finish_rebuild(0, 0); return; }
+      return;                                         // a grid step is planned
+    }
+  }
+
+  // Coordinator block: the largest current degree of an alive vertex among
+  // dsort[lo, hi) (0 if none).
+  __device__ int64_t deg_max_over(int64_t lo, int64_t hi) {
+    int64_t mx = 0;
+    for (int64_t base = lo + threadIdx.x; base < hi; base += (int64_t)kScanU * blockDim.x) {
+      uint32_t x[kScanU];
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = base + (int64_t)q * blockDim.x;
+        x[q] = i < hi ? ldcg(B.st + __ldg(B.dsort + i)) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q)
+        if (is_alive(x[q])) mx = (int64_t)deg_of(x[q]) > mx ? (int64_t)deg_of(x[q]) : mx;
+    }
+    return block_max<int64_t>(mx, S->scr);
   }
 
   __device__ void set_nz_plan() {
     Coord& c = co();
     S->plan.win_lo = 0;
-    S->plan.win_len = c.nz_static ? c.nz_len : c.nz_len;
+    S->plan.win_len = c.nz_len;
     S->plan.pad0 = (c.nz_static ? 2 : 0) | c.nz_sel;
+  }
+
+  // Coordinator: the new maximum D and heavy list of hcount entries are in
+  // place; plan the round's selection.
+  __device__ void finish_rebuild(int32_t D, int64_t hcount) {
+    if (threadIdx.x == 0) {
+      Coord& c = co();
+      c.tau = D >= 2 ? D >> 1 : 1;
+      c.h_len = D > 0 ? hcount : 0;
+      if (D <= 0) c.delta_zero = 1;
+    }
+    __syncthreads();
+    plan_selection(D > 0 ? D : 0);
   }
 
   // Statistics and n_i update after the removal phase, then the next plan.
@@ -589,11 +737,10 @@ struct K {
     });
   }
 
-  // ---------------- heavy list rebuild ------------------------------------------
-  // A: over the non-isolated alive list, count the vertices that are still
-  // alive with a degree > 0 and find the largest degree D.  B: compact that
-  // list and put every survivor with degree >= tau = max(1, D/2) on the heavy
-  // list.  Delta = D exactly.
+  // ---------------- Delta rebuild: grid passes ---------------------------------
+  // Over the compact list (vertex order): A, count the vertices that are still
+  // alive with a degree > 0 and find the largest degree D; B, compact the list
+  // and put every survivor of degree >= tau = max(1, D/2) on the heavy list.
   __device__ int32_t nz_at(int flags, int64_t i) const {
     if (flags & 2) return __ldg(B.nz_static + i);
     return ldcg(((flags & 1) ? B.nz1 : B.nz0) + i);
@@ -632,8 +779,7 @@ struct K {
             Coord& c = co();
             c.nz_total = tot;
             c.d_new = (int32_t)(D > 0 ? D : 0);
-            c.tau = D >= 2 ? (int32_t)(D >> 1) : 1;
-            S->plan.th = c.tau;
+            S->plan.th = D >= 2 ? (int32_t)(D >> 1) : 1;
             C->h_pack = 0;
           }
         }))
@@ -682,13 +828,77 @@ struct K {
         c.nz_sel = (flags & 2) ? 0 : ((flags & 1) ? 0 : 1);
         c.nz_static = 0;
         c.nz_len = c.nz_total;
-        c.h_len = (int64_t)vload(&C->h_pack);
-        c.rebuilds_in_row += 1;
-        if (c.rebuilds_in_row > 3) fail(kErrInternal);
       }
       __syncthreads();
-      plan_selection(co().d_new);
+      finish_rebuild(co().d_new, (int64_t)vload(&C->h_pack));
     });
+  }
+
+  // One segment dsort[win_lo, win_lo + win_len) of the degree-order search:
+  // the largest current degree of an alive vertex in it.
+  __device__ bool rebuild_segment() {
+    int64_t s, e;
+    slice(P().win_lo, P().win_len, &s, &e);
+    int64_t mx = 0;
+    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+      uint32_t x[kScanU];
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+        x[q] = i < e ? ldcg(B.st + __ldg(B.dsort + i)) : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q)
+        if (is_alive(x[q])) mx = (int64_t)deg_of(x[q]) > mx ? (int64_t)deg_of(x[q]) : mx;
+    }
+    mx = block_max<int64_t>(mx, S->scr);
+    if (threadIdx.x == 0) B.blk_b[bid] = mx;
+    return sync(0, [&] {
+      const int64_t m = max_blocks_signed();
+      if (threadIdx.x == 0) {
+        Coord& c = co();
+        c.rb_D = m > c.rb_D ? (int32_t)m : c.rb_D;
+        c.rb_lo = c.rb_hi;
+      }
+      __syncthreads();
+      rebuild_advance();
+    });
+  }
+
+  // The heavy list from dsort[0, win_len): every alive vertex of current
+  // degree >= th (> 0).
+  __device__ bool heavy_fill() {
+    int64_t s, e;
+    slice(0, P().win_len, &s, &e);
+    const int64_t tau = P().th;
+    for (int64_t base = s; base < e; base += (int64_t)blockDim.x * kScanU) {
+      int32_t v[kScanU];
+      uint32_t x[kScanU];
+      int64_t heavy = 0;
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+        v[q] = i < e ? __ldg(B.dsort + i) : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q) {
+        x[q] = v[q] >= 0 ? ldcg(B.st + v[q]) : 0u;
+        if (!(is_alive(x[q]) && deg_of(x[q]) > 0 && (int64_t)deg_of(x[q]) >= tau)) v[q] = -1;
+        heavy += v[q] >= 0 ? 1 : 0;
+      }
+      int64_t htot;
+      int64_t ho = block_exclusive_sum<int64_t>(heavy, S->scr, &htot);
+      if (htot > 0) {
+        if (threadIdx.x == 0) S->bcast[0] = (int64_t)atomicAdd(&C->h_pack, (unsigned long long)htot);
+        __syncthreads();
+        ho += S->bcast[0];
+        __syncthreads();
+      }
+#pragma unroll
+      for (int q = 0; q < kScanU; ++q)
+        if (v[q] >= 0) B.hv[ho++] = v[q];
+    }
+    return sync(1, [&] { finish_rebuild(co().rb_D, (int64_t)vload(&C->h_pack)); });
   }
 
   __device__ int64_t max_blocks_signed() {
@@ -1211,6 +1421,14 @@ __device__ void run_job(K& k, int algo) {
       if (!k.delta_rebuild()) goto out;
       continue;
     }
+    if (S.plan.state == kRebuildDeg) {
+      if (!k.rebuild_segment()) goto out;
+      continue;
+    }
+    if (S.plan.state == kRebuildHeavy) {
+      if (!k.heavy_fill()) goto out;
+      continue;
+    }
     if (S.plan.state == kScanH) {
       if (!k.heavy_scan()) goto out;
       continue;
@@ -1458,6 +1676,8 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
       rb.max_deg = jb.max_deg;
       rb.off = jb.off;
       rb.col = jb.col;
+      rb.dsort = jb.dsort;
+      rb.dge = jb.dge;
       rb.nz_static = jb.nz;
       rb.nz_n = jb.nz_n;
       rb.order = rb.order_w;

@@ -122,6 +122,7 @@ int start_batch(cc_server* sv, Flight& f, std::vector<Request>& reqs) {
     const cc_graph* g = reqs[q].g;
     BatchJob& jb = f.jobs[q];
     jb.off = g->off; jb.col = g->col; jb.nz = g->nz_row; jb.nz_n = g->nz_n;
+    jb.dsort = g->dsort; jb.dge = g->dge;
     jb.n = g->n; jb.nnz = g->nnz; jb.max_deg = g->max_deg;
     jb.seed = reqs[q].seed;
     jb.labels = reqs[q].labels;
