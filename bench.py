@@ -47,8 +47,8 @@ def parse_args(argv=None):
                    help="also time the other workload configurations once each (0 = skip)")
     p.add_argument("--parity", type=int, default=1,
                    help="check the last timed step's labels against the oracle on the full graph (CPU leg)")
-    p.add_argument("--batch-graphs", type=int, default=256,
-                   help="Chung-Lu graphs in the batched-jobs measurement (0 = skip)")
+    p.add_argument("--batch-graphs", type=int, default=4096,
+                   help="Chung-Lu graphs of the batched and served workload (0 = skip the batch leg)")
     p.add_argument("--sec5", type=int, default=1, help="also time the Sec. 5 schedule once per algorithm (0 = skip)")
     p.add_argument("--async-c4", type=int, default=1, help="also time C4 without rounds (Alg. 3) once (0 = skip)")
     p.add_argument("--serve-seconds", type=float, default=2.0,
@@ -284,93 +284,157 @@ def cpu_sample_run(algos, eps, seed_base=7):
     return g.m * len(algos), dt
 
 
-def batch_workload(count: int, base_seed: int = 0):
-    """Chung-Lu graphs (exponent 2.1) with n log-uniform in [1e3, 3e4] and mean
-    degree uniform in [8, 64], seed base + g: a bounded slice of the
-    4,096-graph batch (whose n reaches 1e6)."""
-    import concurrent.futures
+class BatchWorkload:
+    """The batched and served workload: Chung-Lu graphs (exponent 2.1), n
+    log-uniform in [1e3, 1e6], mean degree uniform in [8, 64], seed = g
+    (graphgen.chung_lu_batch_params), generated on the GPU
+    (graphgen.chung_lu_device) and adopted by the library as device CSR.
+    The graphs are admitted in waves of at most `wave_bytes` of CSR; on one
+    GB300 every wave stays resident (about 90 GB for 4,096 graphs)."""
 
-    import graphgen
+    def __init__(self, cc, torch, count: int, wave_bytes: int = 48 << 30):
+        import graphgen
+        self.params = graphgen.chung_lu_batch_params(count)
+        self.graphs, self.tensors, self.waves = [], [], []
+        t0 = time.perf_counter()
+        wave, wbytes = 0, 0
+        for (n, d, seed) in self.params:
+            off, col = graphgen.chung_lu_device(n, d, seed=seed)
+            if wbytes + 4 * col.numel() > wave_bytes and wbytes > 0:
+                self.waves.append(wave)
+                wave, wbytes = 0, 0
+            wave += 1
+            wbytes += 4 * col.numel() + 8 * off.numel()
+            self.tensors.append((off, col))
+            self.graphs.append(cc.Graph(off, col))
+        self.waves.append(wave)
+        torch.cuda.synchronize()
+        self.gen_s = time.perf_counter() - t0
+        self.sum_n = sum(g.n for g in self.graphs)
+        self.sum_m = sum(g.m for g in self.graphs)
+
+    def describe(self):
+        return (f"{len(self.graphs)} Chung-Lu graphs (exponent 2.1), n log-uniform in [1e3, 1e6], mean degree "
+                f"U[8, 64], seed = index; sum n = {self.sum_n}, sum m = {self.sum_m}; generated on the GPU in "
+                f"{self.gen_s:.1f} s, admitted in {len(self.waves)} wave(s) of <= 48 GB of CSR, all resident")
+
+    def host_graph(self, i):
+        import graphgen
+        off, col = self.tensors[i]
+        return graphgen.to_host(off, col)
+
+    def close(self):
+        for g in self.graphs:
+            g.close()
+        self.graphs, self.tensors = [], []
+
+
+def measure_batch(cc, torch, wl: "BatchWorkload", k_perms: int, eps: float, algos=("cw", "c4")):
+    """Jobs/s of the batched engine (every (graph, permutation) job of the
+    workload, best-of-k per graph) against one launch per job, per algorithm.
+    Also returns the jobs kept for the oracle check of the CPU leg."""
     import numpy as np
-    graphgen.build()
-    params = []
-    for g in range(count):
-        r = np.random.default_rng(base_seed + g)
-        params.append((int(round(10 ** (3 + np.log10(30.0) * r.random()))), 8.0 + 56.0 * r.random(), base_seed + g))
-    with concurrent.futures.ThreadPoolExecutor(16) as ex:
-        return list(ex.map(lambda p: graphgen.chung_lu(p[0], p[1], seed=p[2], threads=1), params))
-
-
-def measure_batch(cc, torch, gs, k_perms: int, eps: float, algo: str = "cw"):
-    """Jobs/s of the batched launch against one launch per job."""
-    import numpy as np
-    graphs = [cc.Graph(g.off, g.col) for g in gs]
-    try:
-        seeds = np.arange(len(gs), dtype=np.uint64) * 1000
-        cc.batch_jobs(graphs[:8], algo, eps, seeds[:8], 2)          # warm-up
+    seeds = np.arange(len(wl.graphs), dtype=np.uint64) * 1000
+    out = {"workload": wl.describe(), "graphs": len(wl.graphs), "k_perms": k_perms, "eps": eps,
+           "sum_n": wl.sum_n, "sum_m": wl.sum_m}
+    cc.batch_jobs(wl.graphs[:8], "cw", eps, seeds[:8], 2)           # warm-up
+    torch.cuda.synchronize()
+    # one launch per job on a stratified sample (graphs spread over the size range)
+    order = sorted(range(len(wl.graphs)), key=lambda i: wl.graphs[i].n)
+    sample = order[:: max(1, len(order) // 48)]
+    check = {}
+    for a in algos:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        D, R = cc.batch_jobs(graphs, algo, eps, seeds, k_perms)
+        D, R = cc.batch_jobs(wl.graphs, a, eps, seeds, k_perms)
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
-        jobs = len(gs) * k_perms
-        # one launch per job on a sample of the jobs (same jobs, same results)
-        sample = list(range(0, len(gs), max(1, len(gs) // 64)))
+        jobs = len(wl.graphs) * k_perms
         t0 = time.perf_counter()
         for i in sample:
-            for j in range(k_perms):
-                _, r, d = graphs[i].cluster(algo, eps, int(seeds[i]) + j, want_labels=False)
-                assert (r, d) == (R[i, j], D[i, j])
-        t_single = (time.perf_counter() - t0) / (len(sample) * k_perms)
-        return {"graphs": len(gs), "k_perms": k_perms, "jobs": jobs, "algo": algo, "eps": eps,
-                "jobs_per_s": jobs / t_batch, "ms": t_batch * 1e3,
-                "one_launch_per_job_jobs_per_s": 1.0 / t_single,
-                "speedup_vs_one_launch_per_job": (jobs / t_batch) * t_single,
-                "sum_n": int(sum(g.n for g in gs)), "sum_m": int(sum(g.m for g in gs)),
-                "workload": "Chung-Lu exponent 2.1, n log-uniform [1e3, 3e4], mean degree U[8, 64], best-of-k jobs"}
-    finally:
-        for x in graphs:
-            x.close()
+            _, r, d = wl.graphs[i].cluster(a, eps, int(seeds[i]) + 1, want_labels=False)
+            assert (r, d) == (R[i, 1], D[i, 1])
+        t_single = (time.perf_counter() - t0) / len(sample)
+        # one-launch-per-job time of the whole workload, from the sample's
+        # per-size rate (edges per second of the sampled jobs)
+        sample_m = sum(wl.graphs[i].m for i in sample)
+        t_single_all = t_single * len(sample) / sample_m * wl.sum_m * k_perms
+        out[a] = {"jobs": jobs, "ms": t_batch * 1e3, "jobs_per_s": jobs / t_batch,
+                  "edges_per_s": wl.sum_m * k_perms / t_batch,
+                  "one_launch_per_job_jobs_per_s": jobs / t_single_all,
+                  "speedup_vs_one_launch_per_job": t_single_all / t_batch,
+                  "best_of_k_mean_D_gain": float(np.mean(D.min(1) / np.maximum(D[:, 0], 1))),
+                  "one_launch_sample": f"{len(sample)} graphs across the size range, permutation 1 of each"}
+        pick = [order[0], order[len(order) // 3], order[2 * len(order) // 3], order[-1]]
+        check[a] = [(i, int(seeds[i]) + j, int(R[i, j]), int(D[i, j])) for i in pick for j in (0, k_perms - 1)]
+    return out, check
 
 
-def measure_serving(cc, torch, gs, seconds: float, rate: float = 2000.0, eps: float = 0.5, algo: str = "cw"):
-    """Poisson arrivals at `rate` jobs/s through the serving loop: latency
-    percentiles and achieved throughput, against serving each request with
-    its own launch as it arrives."""
+def measure_serving(cc, torch, wl: "BatchWorkload", seconds: float, rate: float = 2000.0, eps: float = 0.5):
+    """Poisson arrivals at `rate` jobs/s through the serving loop, each request
+    a random graph of the workload, ClusterWild! or C4 with equal odds:
+    latency percentiles, throughput and how many jobs ran at once on the
+    device, against serving each request with its own launch as it arrives."""
     import numpy as np
-    graphs = [cc.Graph(g.off, g.col) for g in gs]
+    graphs = wl.graphs
     rng = np.random.default_rng(2000)
     nreq = max(1, int(rate * seconds))
     arrivals = np.cumsum(rng.exponential(1.0 / rate, nreq))
-    which = rng.integers(0, len(gs), nreq)
-    try:
-        with cc.Server(mem_budget=8 << 30, max_batch=512) as srv:
-            srv.wait(srv.submit(graphs[0], algo, eps, 1))            # warm-up
-            t0 = time.perf_counter()
-            tickets = []
-            for q in range(nreq):
-                while time.perf_counter() - t0 < arrivals[q]:
-                    pass
-                tickets.append(srv.submit(graphs[int(which[q])], algo, eps, 77 + q))
-            lat = np.array([srv.wait(t)[2] for t in tickets])
-            t_total = time.perf_counter() - t0
-        # one launch per request, served in arrival order
+    which = rng.integers(0, len(graphs), nreq)
+    algo = np.where(rng.random(nreq) < 0.5, "cw", "c4")
+    with cc.Server(mem_budget=48 << 30, max_batch=512) as srv:
+        srv.wait(srv.submit(graphs[0], "cw", eps, 1))            # warm-up
         t0 = time.perf_counter()
-        lat1 = []
-        for q in range(min(nreq, 400)):
+        tickets = []
+        for q in range(nreq):
             while time.perf_counter() - t0 < arrivals[q]:
                 pass
-            graphs[int(which[q])].cluster(algo, eps, 77 + q, want_labels=False)
-            lat1.append((time.perf_counter() - t0 - arrivals[q]) * 1e3)
-        lat1 = np.array(lat1)
-        return {"rate_jobs_per_s": rate, "requests": nreq, "throughput_jobs_per_s": nreq / t_total,
-                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                "one_launch_per_job": {"requests": int(lat1.size), "p50_ms": float(np.percentile(lat1, 50)),
-                                       "p99_ms": float(np.percentile(lat1, 99))},
-                "algo": algo, "eps": eps}
-    finally:
-        for x in graphs:
-            x.close()
+            tickets.append(srv.submit(graphs[int(which[q])], str(algo[q]), eps, 77 + q))
+        res = [srv.wait(t) for t in tickets]
+        t_total = time.perf_counter() - t0
+        times = [srv.device_times(t) for t in tickets]
+    lat = np.array([r[2] for r in res])
+    # jobs running at once on the device (from the device clock stamps)
+    ev = sorted([(a, 1) for a, b in times if a > 0] + [(b, -1) for a, b in times if a > 0])
+    cur = peak = 0
+    for _, s in ev:
+        cur += s
+        peak = max(peak, cur)
+    # one launch per request, served in arrival order
+    t0 = time.perf_counter()
+    lat1 = []
+    for q in range(min(nreq, 400)):
+        while time.perf_counter() - t0 < arrivals[q]:
+            pass
+        graphs[int(which[q])].cluster(str(algo[q]), eps, 77 + q, want_labels=False)
+        lat1.append((time.perf_counter() - t0 - arrivals[q]) * 1e3)
+    lat1 = np.array(lat1)
+    small = np.array([graphs[int(i)].n <= 1 << 16 for i in which])
+    return {"workload": wl.describe(), "rate_jobs_per_s": rate, "requests": nreq,
+            "throughput_jobs_per_s": nreq / t_total,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_small_graphs": float(np.percentile(lat[small], 50)) if small.any() else None,
+            "p50_ms_large_graphs": float(np.percentile(lat[~small], 50)) if (~small).any() else None,
+            "peak_jobs_in_flight_on_device": peak,
+            "one_launch_per_job": {"requests": int(lat1.size), "p50_ms": float(np.percentile(lat1, 50)),
+                                   "p99_ms": float(np.percentile(lat1, 99))},
+            "algos": "cw and c4, equal odds", "eps": eps}
+
+
+def batch_oracle_check(wl: "BatchWorkload", check, eps):
+    """Sampled batch jobs (smallest, two middle and the largest graph; first
+    and last permutation) against the oracle: rounds and disagreements."""
+    import oracle
+    oracle.build()
+    out = []
+    for a, items in check.items():
+        for i, seed, r, d in items:
+            g = wl.host_graph(i)
+            order = oracle.permutation(g.n, seed)
+            lab, orr, _, _ = oracle.rounds(g.off, g.col, order, 1 if a == "c4" else 2, eps)
+            od = oracle.disagreements(g.off, g.col, lab)
+            out.append({"algo": a, "graph": i, "n": g.n, "seed": seed, "ok": (orr, od) == (r, d)})
+    return {"jobs_checked": len(out), "all_equal": all(x["ok"] for x in out), "jobs": out}
 
 
 def _time_clusterings(graph, algo, eps, seeds, labels):
@@ -610,13 +674,15 @@ def run_ours(args):
     if rank == 0 and args.configs:
         configs = measure_configs(cc, torch, graph, labels, peak)
 
-    batch = serve = None
+    batch = serve = batch_check = wl = None
     if rank == 0 and (args.batch_graphs > 0 or args.serve_seconds > 0):
-        bgs = batch_workload(max(args.batch_graphs, 64))
+        del labels_of, labels
+        graph.close()                         # room for the batch workload
+        wl = BatchWorkload(cc, torch, max(args.batch_graphs, 64))
         if args.batch_graphs > 0:
-            batch = measure_batch(cc, torch, bgs[:args.batch_graphs], 8, args.eps)
+            batch, batch_check = measure_batch(cc, torch, wl, 8, args.eps)
         if args.serve_seconds > 0:
-            serve = measure_serving(cc, torch, bgs[:64], args.serve_seconds)
+            serve = measure_serving(cc, torch, wl, args.serve_seconds)
 
     cpu = parity = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -629,6 +695,10 @@ def run_ours(args):
         # the timed step's output on the full workload against the oracle
         if args.parity:
             parity = oracle_parity(g, last_step, args.eps)
+            if batch_check:
+                parity["batch"] = batch_oracle_check(wl, batch_check, args.eps)
+    if wl is not None:
+        wl.close()
 
     if rank == 0:
         line = {

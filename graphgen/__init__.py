@@ -169,6 +169,48 @@ def chung_lu_batch_params(count: int = 4096, base_seed: int = 0):
     return out
 
 
+def chung_lu_device(n: int, d: float, beta: float = 2.1, seed: int = 0, device="cuda"):
+    """Chung-Lu graph generated on a GPU with torch (for batches of thousands
+    of graphs, where the host generator would take minutes): the same weights
+    as chung_lu (w_i proportional to (i+1)^(-1/(beta-1)), scaled to mean degree
+    d, capped at sqrt(n d)), round(n d / 2) endpoint pairs drawn by inverse
+    CDF from torch's seeded uniforms, self loops dropped, both directions
+    kept, duplicates merged.  Returns (off int64[n+1], col int32[nnz]) as
+    device tensors; to_host() turns them into a Graph.  The graph depends on
+    the seed and on torch's generator, so it is reproducible on one torch
+    version; the oracle reads the same arrays through to_host()."""
+    import torch
+    dev = torch.device(device)
+    i = torch.arange(1, n + 1, dtype=torch.float64, device=dev)
+    w = i.pow(-1.0 / (beta - 1.0))
+    w = torch.clamp(w * (d * n / float(w.sum())), max=float(np.sqrt(n * d)))
+    cdf = torch.cumsum(w, 0)
+    acc = float(cdf[-1])
+    m = int(round(n * d / 2.0))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(int(seed) & (2**63 - 1))
+    ends = []
+    for _ in range(2):
+        x = torch.rand(m, dtype=torch.float64, device=dev, generator=gen) * acc
+        ends.append(torch.clamp(torch.searchsorted(cdf, x, right=True), max=n - 1))
+    u, v = ends
+    keep = u != v
+    u, v = u[keep], v[keep]
+    keys = torch.cat([u * n + v, v * n + u])
+    del u, v, keep, ends
+    keys = torch.unique(keys, sorted=True)
+    rows = keys // n
+    col = (keys - rows * n).to(torch.int32)
+    off = torch.zeros(n + 1, dtype=torch.int64, device=dev)
+    off[1:] = torch.cumsum(torch.bincount(rows, minlength=n), 0)
+    return off, col
+
+
+def to_host(off, col, name: str = "") -> Graph:
+    """Host Graph from device CSR tensors (chung_lu_device)."""
+    return Graph(off.cpu().numpy(), col.cpu().numpy(), None, name)
+
+
 def workload(name: str, threads: int = 0) -> Graph:
     """'er10k' | 'planted1m' | 'rmat24' | 'rmat26' | 'rmat<scale>'."""
     if name == "er10k":

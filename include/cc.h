@@ -269,13 +269,22 @@ int cc_disagreements_static(int64_t n, const int64_t* row_offsets, const int32_t
 /*
  * Serving loop with continuous batching.  cc_server_submit queues a request
  * (graph g, algo, eps, seed) and returns a ticket at once.  A dispatcher
- * thread starts the waiting requests as one batched launch (one thread block
- * per request) on one of three streams as soon as a stream is free and the
- * device-memory budget covers the batch's scratch, so requests that arrive
- * while others run are admitted and overlap with them.  Graphs stay resident
- * (they are the caller's, and must outlive their requests); graphs above 2^16
- * vertices run on the whole GPU one at a time.  The result of a request is
- * exactly that of cc_cluster with the same arguments.  algo: CC_ALGO_C4 ..
+ * thread starts the waiting requests of one size class as one launch on one
+ * of sixteen streams as soon as a stream is free and the device-memory budget
+ * covers the launch's scratch, so requests that arrive while others run are
+ * admitted and their work overlaps on the device with the work in flight.
+ * Size classes: up to 2^16 vertices one thread block per request; up to 2^21
+ * one team of eight blocks per request (cooperative launches of up to
+ * sixteen teams, two such launches in flight at a time, together at most two
+ * thirds of the GPU); larger graphs the whole
+ * GPU, one request at a time, on a worker thread of their own.  The
+ * dispatcher never waits for the GPU (results come back by asynchronous
+ * copies into pinned host memory).  A launch that fails fails its own
+ * requests only.  Graphs stay resident (they are the caller's, must outlive
+ * their requests, and must not be used by the caller while a request on them
+ * is pending; submit does not wait for the graph's stream).  The result of a
+ * request is exactly that of
+ * cc_cluster with the same arguments.  algo: CC_ALGO_C4 ..
  * CC_ALGO_CLUSTERWILD_EST (CC_ALGO_C4_ASYNC is CC_ERR_INVALID_ARG here).
  *   mem_budget   bytes of device memory for batch scratch (a request whose
  *                scratch alone exceeds it fails with CC_ERR_OOM).
@@ -283,8 +292,11 @@ int cc_disagreements_static(int64_t n, const int64_t* row_offsets, const int32_t
  *   labels_out   device int32[n] or NULL.
  * cc_server_poll returns CC_ERR_BUSY while the request is pending;
  * cc_server_wait blocks (at most 10 minutes).  latency_ms = time from submit
- * to completion as seen by the dispatcher.  cc_server_destroy finishes the
- * queued work first.  A server is thread safe.
+ * to completion as seen by the dispatcher.  cc_server_device_times gives the
+ * device clock (%globaltimer, ns) at which a finished request's job started
+ * and ended on the GPU (-1 for requests that ran on the whole GPU), so that
+ * callers can see which requests overlapped; CC_ERR_BUSY while pending.
+ * cc_server_destroy finishes the queued work first.  A server is thread safe.
  */
 typedef struct cc_server cc_server;
 int cc_server_create(size_t mem_budget, int32_t max_batch, cc_server** out);
@@ -294,6 +306,7 @@ int cc_server_poll(cc_server* s, int64_t ticket, int32_t* rounds, int64_t* disag
                    double* latency_ms);
 int cc_server_wait(cc_server* s, int64_t ticket, int32_t* rounds, int64_t* disagreements,
                    double* latency_ms);
+int cc_server_device_times(cc_server* s, int64_t ticket, int64_t* start_ns, int64_t* end_ns);
 int cc_server_destroy(cc_server* s);
 
 /*

@@ -139,6 +139,7 @@ struct BatchJob {
   int32_t* labels;      // optional device int32[n]: center vertex id of each vertex
   int64_t rounds;       // result
   int64_t D;            // result: disagreements
+  int64_t t0, t1;       // result: device clock (%globaltimer, ns) at the job's start and end
 };
 
 // Largest co-resident grid of the batched kernel on this device.

@@ -1683,6 +1683,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
       rb.order = rb.order_w;
       rb.stats = nullptr;
       rb.stats_cap = 0;
+      if (k.bid == 0) jobs[j].t0 = (int64_t)globaltimer_ns();   // device clock at the job's start
     }
     __syncthreads();
     // zero the permutation counters, reset the control block (not the barrier counters)
@@ -1737,6 +1738,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
             jb.rounds = S.co.round;
             jb.D = jb.nnz / 2 - 2 * (int64_t)vload(&C->mc) - (int64_t)vload(&C->mm) + (int64_t)vload(&C->pairs);
             jb.err = done ? 0 : kErrInternal;
+            jb.t1 = (int64_t)globaltimer_ns();
             S.plan.state = kDone;
           }
         }))

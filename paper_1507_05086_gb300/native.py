@@ -105,6 +105,8 @@ def load(build_if_missing: bool = True):
         lib.cc_server_poll.argtypes = [vp, i64, vp, vp, vp]
         lib.cc_server_wait.restype = ci
         lib.cc_server_wait.argtypes = [vp, i64, vp, vp, vp]
+        lib.cc_server_device_times.restype = ci
+        lib.cc_server_device_times.argtypes = [vp, i64, vp, vp]
         lib.cc_server_destroy.restype = ci
         lib.cc_server_destroy.argtypes = [vp]
         lib.cc_batch_run.restype = ci
@@ -296,8 +298,9 @@ class Server:
     """Serving loop with continuous batching (``cc_server_*``).
 
     ``submit`` returns a ticket at once; requests waiting when a stream frees
-    up run together as one batched launch, overlapping with earlier batches,
-    within a device-memory budget for their scratch.
+    up run together as one batched launch (per size class), overlapping on
+    the device with earlier batches, within a device-memory budget for their
+    scratch.
     """
 
     def __init__(self, mem_budget: int = 4 << 30, max_batch: int = 1024):
@@ -328,6 +331,14 @@ class Server:
         _check("cc_server_wait", self._lib.cc_server_wait(self._h, ticket, ctypes.byref(r), ctypes.byref(d),
                                                           ctypes.byref(ms)))
         return r.value, d.value, ms.value
+
+    def device_times(self, ticket: int):
+        """(start_ns, end_ns) of a finished request's job on the device clock
+        (-1, -1 for requests that ran on the whole GPU)."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check("cc_server_device_times", self._lib.cc_server_device_times(self._h, ticket, ctypes.byref(a),
+                                                                           ctypes.byref(b)))
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "_h", None):

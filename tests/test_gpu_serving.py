@@ -100,3 +100,86 @@ def test_admission_by_memory(cc, gg):
             assert ei.value.status == -3
     finally:
         graph.close()
+
+
+def test_batches_overlap_on_the_device_across_size_classes(cc, ora, gg):
+    """Continuous batching: requests that arrive while an earlier batch runs
+    start on the device before that batch ends (device clock stamps of every
+    job), medium graphs run as teams of blocks and a graph above 2^21 vertices
+    on the whole GPU at the same time, and every result equals the standalone
+    clustering (and the oracle for a sample)."""
+    import torch
+    small = [gg.chung_lu(n, 16.0, seed=90 + i) for i, n in enumerate((30000, 45000, 60000))]
+    medium = gg.chung_lu(300_000, 12.0, seed=95)
+    large = gg.rmat(22, 8, seed=96)
+    assert large.n > 1 << 21 and (1 << 16) < medium.n <= (1 << 21)
+    graphs = [cc.Graph(g.off, g.col) for g in small + [medium, large]]
+    gsets = small + [medium, large]
+    reqs = []
+    try:
+        with cc.Server(mem_budget=16 << 30, max_batch=128) as srv:
+            srv.wait(srv.submit(graphs[0], "cw", 0.1, 1))          # warm-up
+            wave1, wave2 = [], []
+            # wave 1: long jobs (a small eps means many rounds); wave 2 (another
+            # algorithm, so never the same launch) arrives right behind it
+            for q in range(96):
+                i = q % 3
+                reqs.append((i, "cw", 0.02, 1000 + q))
+                wave1.append(srv.submit(graphs[i], "cw", 0.02, 1000 + q))
+            for q in range(48):
+                i = q % 3
+                reqs.append((i, "c4", 0.5, 5000 + q))
+                wave2.append(srv.submit(graphs[i], "c4", 0.5, 5000 + q))
+            t_mid = srv.submit(graphs[3], "c4", 0.5, 7)              # a team job
+            t_big = srv.submit(graphs[4], "cw", 0.5, 8)              # the whole GPU
+            res = [srv.wait(t) for t in wave1 + wave2]
+            r_mid, r_big = srv.wait(t_mid), srv.wait(t_big)
+            times1 = [srv.device_times(t) for t in wave1]
+            times2 = [srv.device_times(t) for t in wave2]
+            tm = srv.device_times(t_mid)
+            assert srv.device_times(t_big) == (-1, -1)
+        assert all(a > 0 and b >= a for a, b in times1 + times2 + [tm])
+        end1 = max(b for _, b in times1)
+        start2 = min(a for a, _ in times2)
+        assert start2 < end1, ("the second wave must start on the device while the first still runs",
+                               (end1 - min(a for a, _ in times1)) / 1e6, (start2 - end1) / 1e6)
+        for (i, algo, eps, seed), (r, d, _) in zip(reqs, res):
+            _, r2, d2 = graphs[i].cluster(algo, eps, seed, want_labels=False)
+            assert (r, d) == (r2, d2), (i, algo, seed)
+        _, r2, d2 = graphs[3].cluster("c4", 0.5, 7, want_labels=False)
+        assert (r_mid[0], r_mid[1]) == (r2, d2)
+        _, r2, d2 = graphs[4].cluster("cw", 0.5, 8, want_labels=False)
+        assert (r_big[0], r_big[1]) == (r2, d2)
+        g = medium
+        kc = ora.kwik(g.off, g.col, ora.permutation(g.n, 7))
+        assert r_mid[1] == ora.disagreements(g.off, g.col, kc)
+        for k in (0, 50, 100, 140):
+            i, algo, eps, seed = reqs[k]
+            g = gsets[i]
+            olab, orr, _, _ = ora.rounds(g.off, g.col, ora.permutation(g.n, seed), 1 if algo == "c4" else 2, eps)
+            assert res[k][0] == orr and res[k][1] == ora.disagreements(g.off, g.col, olab)
+    finally:
+        for x in graphs:
+            x.close()
+
+
+def test_a_failed_batch_does_not_stop_the_server(cc, gg):
+    """A request whose scratch can never fit fails alone; later requests are
+    served normally."""
+    g_small = gg.chung_lu(2000, 8.0, seed=1)
+    g_big = gg.chung_lu(60000, 16.0, seed=2)
+    a, b = cc.Graph(g_small.off, g_small.col), cc.Graph(g_big.off, g_big.col)
+    try:
+        with cc.Server(mem_budget=4 << 20, max_batch=8) as srv:
+            t_bad = srv.submit(b, "cw", 0.5, 3)
+            with pytest.raises(cc.CCError) as ei:
+                srv.wait(t_bad)
+            assert ei.value.status == -3
+            ts = [srv.submit(a, "cw", 0.5, s) for s in range(5)]
+            res = [srv.wait(t) for t in ts]
+        for s, (r, d, _) in enumerate(res):
+            _, r2, d2 = a.cluster("cw", 0.5, s, want_labels=False)
+            assert (r, d) == (r2, d2)
+    finally:
+        a.close()
+        b.close()
