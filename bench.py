@@ -41,7 +41,7 @@ def parse_args(argv=None):
     p.add_argument("--workload", default="rmat26")
     p.add_argument("--eps", type=float, default=0.5)
     p.add_argument("--algos", default="cw,c4")
-    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--e2e-steps", type=int, default=4)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--configs", type=int, default=1,
                    help="also time the other workload configurations once each (0 = skip)")
@@ -437,6 +437,66 @@ def batch_oracle_check(wl: "BatchWorkload", check, eps):
     return {"jobs_checked": len(out), "all_equal": all(x["ok"] for x in out), "jobs": out}
 
 
+def measure_e2e(cc, torch, g, algos, eps, steps, rank):
+    """End to end through the C ABI with host buffers.  Every step uploads the
+    graph from pinned host memory (cc_graph_create: copy and validation),
+    runs one clustering per algorithm with labels returned to pinned host
+    memory, and destroys the graph.  Timed two ways, after one untimed step
+    (the library's pool grows to the graph's size once):
+    * pipelined (the value): the next step's graph is created by a second
+      host thread on its own stream while this step's clusterings run, the
+      way a caller processing a stream of graphs would overlap them; the
+      first step's upload is inside the timed region and not overlapped;
+    * serial: create, cluster, destroy one step after the other.
+    Wall clock around device-wide synchronisation (several streams)."""
+    import concurrent.futures
+    off_h = torch.from_numpy(g.off).pin_memory()
+    col_h = torch.from_numpy(g.col).pin_memory()
+    lab_h = {a: torch.empty(max(g.n, 1), dtype=torch.int32).pin_memory() for a in algos}
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    dev = torch.cuda.current_device()
+
+    def create(i):
+        torch.cuda.set_device(dev)                        # the device is per host thread
+        return cc.Graph(off_h.numpy(), col_h.numpy(), stream=streams[i % 2].cuda_stream)
+
+    def cluster_all(gh, step):
+        for a, seed in zip(algos, step_seeds(rank, step, len(algos))):
+            gh.cluster(a, eps, seed, labels_out=lab_h[a].numpy())
+
+    with create(0) as gh:                                  # untimed: pool growth
+        cluster_all(gh, 9_999)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(steps):
+        with create(s) as gh:
+            cluster_all(gh, 10_000 + s)
+    torch.cuda.synchronize()
+    serial_ms = (time.perf_counter() - t0) * 1e3 / steps
+    with concurrent.futures.ThreadPoolExecutor(1) as ex:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nxt = ex.submit(create, 0)
+        for s in range(steps):
+            gh = nxt.result()
+            if s + 1 < steps:
+                nxt = ex.submit(create, s + 1)
+            cluster_all(gh, 20_000 + s)
+            gh.close()
+        torch.cuda.synchronize()
+        pipe_ms = (time.perf_counter() - t0) * 1e3 / steps
+    m = g.m
+    return {"value": m * len(algos) / (pipe_ms / 1e3), "unit": "edges/s",
+            "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz,
+            "d2h_bytes_per_step": (4 * g.n + 16) * len(algos),
+            "ms_per_step": pipe_ms, "steps": steps,
+            "serial": {"value": m * len(algos) / (serial_ms / 1e3), "ms_per_step": serial_ms},
+            "what": "per step: cc_graph_create from pinned host CSR (copy + validation), one C4 and one "
+                    "ClusterWild! cc_cluster with labels to pinned host memory, cc_graph_destroy; the next "
+                    "step's upload overlapped with this step's clusterings by a second host thread "
+                    "(serial: no overlap); after one untimed step; measured before the device-resident steps"}
+
+
 def _time_clusterings(graph, algo, eps, seeds, labels):
     """Device time (permutation + rounds + labels, CUDA events) of one
     clustering per seed after one warm-up; returns the means and the last
@@ -550,33 +610,7 @@ def run_ours(args):
     # alone does not slow them, and the cause was not identified)
     e2e = None
     if args.e2e_steps > 0:
-        off_h = torch.from_numpy(g.off).pin_memory()
-        col_h = torch.from_numpy(g.col).pin_memory()
-        lab_h = torch.empty(max(g.n, 1), dtype=torch.int32).pin_memory()
-        # one untimed step first: the library's memory pool grows to the
-        # graph's size once (a one-time mapping cost)
-        with cc.Graph(off_h.numpy(), col_h.numpy()) as gh:
-            for a, seed in zip(algos, step_seeds(rank, 9_999, len(algos))):
-                gh.cluster(a, args.eps, seed, labels_out=lab_h.numpy())
-        torch.cuda.synchronize()
-        es = torch.cuda.Event(enable_timing=True)
-        ee = torch.cuda.Event(enable_timing=True)
-        es.record()
-        for s in range(args.e2e_steps):
-            with cc.Graph(off_h.numpy(), col_h.numpy()) as gh:
-                for a, seed in zip(algos, step_seeds(rank, 10_000 + s, len(algos))):
-                    gh.cluster(a, args.eps, seed, labels_out=lab_h.numpy())
-        ee.record()
-        torch.cuda.synchronize()
-        e_ms = es.elapsed_time(ee)
-        e2e = {"value": m * len(algos) * args.e2e_steps / (e_ms / 1e3), "unit": "edges/s",
-               "h2d_bytes_per_step": 8 * (g.n + 1) + 4 * g.nnz,
-               "d2h_bytes_per_step": (4 * g.n + 16) * len(algos),
-               "ms_per_step": e_ms / args.e2e_steps,
-               "what": "per step: cc_graph_create from pinned host CSR (copy + validation), one C4 and one "
-                       "ClusterWild! cc_cluster with labels to pinned host memory, cc_graph_destroy; "
-                       "after one untimed step; measured before the device-resident steps"}
-        del off_h, col_h, lab_h
+        e2e = measure_e2e(cc, torch, g, algos, args.eps, args.e2e_steps, rank)
 
     graph = cc.Graph(g.off, g.col)
     graph.set_timing(True)
