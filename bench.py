@@ -43,6 +43,8 @@ def parse_args(argv=None):
     p.add_argument("--algos", default="cw,c4")
     p.add_argument("--e2e-steps", type=int, default=4)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tune", type=int, default=1,
+                   help="pick the schedule settings with the autotuner (cached per device and graph class)")
     p.add_argument("--configs", type=int, default=1,
                    help="also time the other workload configurations once each (0 = skip)")
     p.add_argument("--parity", type=int, default=1,
@@ -614,6 +616,12 @@ def run_ours(args):
 
     graph = cc.Graph(g.off, g.col)
     graph.set_timing(True)
+    # schedule settings for this graph class on this device: from the
+    # autotuner's cache, else tuned now (no setting changes a result)
+    tuning = {}
+    if args.tune:
+        from paper_1507_05086_gb300 import autotune
+        tuning["rounds"] = autotune.tune_rounds(graph, tuple(algos), args.eps, budget_s=30.0)
     # one label buffer per algorithm, so that the last timed step's labels of
     # both can be checked against the oracle after the timed region
     labels_of = {a: torch.empty(max(g.n, 1), dtype=torch.int32, device="cuda") for a in algos}
@@ -713,6 +721,10 @@ def run_ours(args):
         del labels_of, labels
         graph.close()                         # room for the batch workload
         wl = BatchWorkload(cc, torch, max(args.batch_graphs, 64))
+        if args.tune:
+            from paper_1507_05086_gb300 import autotune
+            # size classes and team size, timed on every eighth graph of the batch
+            tuning["batch"] = autotune.tune_batch(wl.graphs[::8], "cw", args.eps, k_perms=2, budget_s=60.0)
         if args.batch_graphs > 0:
             batch, batch_check = measure_batch(cc, torch, wl, 8, args.eps)
         if args.serve_seconds > 0:
@@ -759,6 +771,7 @@ def run_ours(args):
             "random_access": random_access,
             "cpu_baseline": cpu,
             "parity": parity,
+            "tuning": tuning,
             "configs": configs,
             "batch": batch,
             "serve": serve,

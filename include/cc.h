@@ -310,6 +310,51 @@ int cc_server_device_times(cc_server* s, int64_t ticket, int64_t* start_ns, int6
 int cc_server_destroy(cc_server* s);
 
 /*
+ * Schedule settings (the autotuner's knobs).  None of them changes any
+ * result -- labels, rounds and disagreements are the same under every valid
+ * setting -- only how the work is cut into pieces and where it runs.  The
+ * paper has no counterpart (its implementation ran on CPU threads).
+ *   walk_batches     edge walker: 128-entry batches per warp chunk, 1..8 (4)
+ *   prefetch_ahead   edge walker: batches of a long row prefetched into L2,
+ *                    0..8 (2)
+ *   inline_heavy     exact Delta: heavy lists up to this long are scanned
+ *                    inside the grid barrier by one block, 0..65536 (8192)
+ *   inline_decide    C4: blocked lists up to this long are decided inside the
+ *                    barrier, 0..65536 (4096)
+ *   inline_rebuild   Delta rebuild: degree-order segments up to this long are
+ *                    read inside the barrier, 0..65536 (8192)
+ *   heavy_shift      heavy-list threshold tau = max(1, Delta >> heavy_shift),
+ *                    1..4 (1)
+ *   batch_small_n    batched jobs and served requests: one thread block per
+ *                    job up to this many vertices, 1..2^20 (65536)
+ *   batch_team_n     one team of blocks per job up to this many vertices,
+ *                    >= batch_small_n, <= 2^24 (2^21)
+ *   batch_team_blocks  blocks per team, 2..16 (8)
+ * cc_tuning_default fills the defaults (in brackets).  cc_graph_set_tuning
+ * sets the round-kernel settings (the first six) for the clusterings of one
+ * graph; cc_set_batch_tuning sets them, and the size classes, for every
+ * later cc_batch_jobs / cc_batch_run call and every server created later
+ * (process-wide).  Out-of-range values: CC_ERR_INVALID_ARG, nothing changed.
+ */
+typedef struct cc_tuning {
+  int32_t walk_batches;
+  int32_t prefetch_ahead;
+  int32_t inline_heavy;
+  int32_t inline_decide;
+  int32_t inline_rebuild;
+  int32_t heavy_shift;
+  int64_t batch_small_n;
+  int64_t batch_team_n;
+  int32_t batch_team_blocks;
+  int32_t reserved;          /* 0 */
+} cc_tuning;
+int cc_tuning_default(cc_tuning* out);
+int cc_graph_set_tuning(cc_graph* g, const cc_tuning* t);
+int cc_graph_get_tuning(const cc_graph* g, cc_tuning* out);
+int cc_set_batch_tuning(const cc_tuning* t);
+int cc_get_batch_tuning(cc_tuning* out);
+
+/*
  * Device memory.  Every device allocation of the library (graphs, clustering
  * workspaces, batch and serving scratch) comes from one memory pool per GPU,
  * owned by the library, on the caller's stream (stream-ordered).  Memory a

@@ -5,8 +5,10 @@ The bulk-synchronous rounds of "Parallel Correlation Clustering on Big Graphs"
 sm_103a CUDA kernels behind the C ABI of ``include/cc.h``.  This package is a
 thin ctypes binding over that library.
 """
-from .native import (ALGOS, C4, CLUSTERWILD, CCError, Graph, ROUND_STAT_FIELDS, Server, batch_jobs,
-                     batch_run, lib_path, load, release_memory)
+from .native import (ALGOS, C4, CLUSTERWILD, CCError, Graph, ROUND_STAT_FIELDS, Server, Tuning, batch_jobs,
+                     batch_run, default_tuning, get_batch_tuning, lib_path, load, release_memory,
+                     set_batch_tuning)
 
-__all__ = ["ALGOS", "C4", "CLUSTERWILD", "CCError", "Graph", "ROUND_STAT_FIELDS", "Server", "batch_jobs",
-           "batch_run", "lib_path", "load", "release_memory"]
+__all__ = ["ALGOS", "C4", "CLUSTERWILD", "CCError", "Graph", "ROUND_STAT_FIELDS", "Server", "Tuning", "batch_jobs",
+           "batch_run", "default_tuning", "get_batch_tuning", "lib_path", "load", "release_memory",
+           "set_batch_tuning"]

@@ -66,11 +66,49 @@ extern "C" int cc_release_memory(void) {
 }
 
 namespace {
-// batched size classes: up to kBatchSmallN vertices one block runs a job, up
-// to kBatchTeamN a team of kBatchTeamBlocks blocks, beyond that the whole grid
+// batched size classes (defaults): up to batch_small_n vertices one block
+// runs a job, up to batch_team_n a team of batch_team_blocks blocks, beyond
+// that the whole grid
 constexpr int64_t kBatchSmallN = 1 << 16;
 constexpr int64_t kBatchTeamN = 1 << 21;
 constexpr int kBatchTeamBlocks = 8;
+
+cc_tuning public_default_tuning() {
+  const Tuning d = default_tuning();
+  cc_tuning t{};
+  t.walk_batches = d.walk_batches;
+  t.prefetch_ahead = d.prefetch_ahead;
+  t.inline_heavy = d.inline_heavy;
+  t.inline_decide = d.inline_decide;
+  t.inline_rebuild = d.inline_rebuild;
+  t.heavy_shift = d.heavy_shift;
+  t.batch_small_n = kBatchSmallN;
+  t.batch_team_n = kBatchTeamN;
+  t.batch_team_blocks = kBatchTeamBlocks;
+  t.reserved = 0;
+  return t;
+}
+
+bool tuning_valid(const cc_tuning& t) {
+  return t.walk_batches >= 1 && t.walk_batches <= 8 && t.prefetch_ahead >= 0 && t.prefetch_ahead <= 8 &&
+         t.inline_heavy >= 0 && t.inline_heavy <= 65536 && t.inline_decide >= 0 && t.inline_decide <= 65536 &&
+         t.inline_rebuild >= 0 && t.inline_rebuild <= 65536 && t.heavy_shift >= 1 && t.heavy_shift <= 4 &&
+         t.batch_small_n >= 1 && t.batch_small_n <= (1 << 20) && t.batch_team_n >= t.batch_small_n &&
+         t.batch_team_n <= (1 << 24) && t.batch_team_blocks >= 2 && t.batch_team_blocks <= 16 && t.reserved == 0;
+}
+
+Tuning device_tuning(const cc_tuning& t) {
+  return Tuning{t.walk_batches, t.prefetch_ahead, t.inline_heavy, t.inline_decide, t.inline_rebuild, t.heavy_shift};
+}
+
+std::mutex g_tune_mu;
+bool g_batch_tuning_set = false;
+cc_tuning g_batch_tuning;
+
+cc_tuning batch_tuning() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_batch_tuning_set ? g_batch_tuning : public_default_tuning();
+}
 }  // namespace
 
 
@@ -465,6 +503,7 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
     return cluster_async(g, seed, labels_out, rounds_out, disagreements_out, stats, stats_cap, stats_len);
   RoundBuffers b;
   rounds_carve(g->round_ws, g->n, g->max_deg, g->grid, &b);
+  b.tune = g->tune;
   b.n = g->n;
   b.nnz = g->nnz;
   b.max_deg = g->max_deg;
@@ -615,17 +654,18 @@ int run_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, con
       jb.D = 0;
     }
   // size classes: one block per job, eight-block teams, or the whole grid
+  const cc_tuning tune = batch_tuning();
   std::vector<int64_t> cls[3];
   for (int64_t q = 0; q < njobs; ++q) {
     const int64_t n = jobs[(size_t)q].n;
-    cls[n <= kBatchSmallN ? 0 : (n <= kBatchTeamN ? 1 : 2)].push_back(q);
+    cls[n <= tune.batch_small_n ? 0 : (n <= tune.batch_team_n ? 1 : 2)].push_back(q);
   }
   const int grid0 = batch_grid_size(gs[0]->device);
   for (int c = 0; c < 2; ++c) {
     std::vector<int64_t>& ids = cls[c];
     if (ids.empty()) continue;
     std::sort(ids.begin(), ids.end(), [&](int64_t a, int64_t b2) { return jobs[(size_t)a].n > jobs[(size_t)b2].n; });
-    const int team = c == 0 ? 1 : kBatchTeamBlocks;
+    const int team = c == 0 ? 1 : tune.batch_team_blocks;
     const int teams = grid0 / team;
     if (teams < 1) return CC_ERR_INTERNAL;
     const int grid = teams * team;
@@ -636,6 +676,7 @@ int run_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, con
     std::vector<RoundBuffers> slots((size_t)teams);
     for (int t = 0; t < teams; ++t) {
       batch_slot_carve(static_cast<char*>(ws) + slot * (size_t)t, n_max, team, &slots[(size_t)t]);
+      slots[(size_t)t].tune = device_tuning(tune);
       CC_TRY(cudaMemsetAsync(slots[(size_t)t].ctl, 0, sizeof(Ctl), s));
     }
     std::vector<BatchJob> sub(ids.size());
@@ -675,6 +716,61 @@ int run_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, con
 }  // namespace
 
 extern "C" {
+
+}  // extern "C"
+
+namespace ccg {
+// The process-wide batch settings (cc_set_batch_tuning) as the server reads
+// them when it is created.
+Tuning batch_settings(int64_t* small_n, int64_t* team_n, int* team_blocks) {
+  const cc_tuning t = batch_tuning();
+  *small_n = t.batch_small_n;
+  *team_n = t.batch_team_n;
+  *team_blocks = t.batch_team_blocks;
+  return device_tuning(t);
+}
+}  // namespace ccg
+
+extern "C" {
+
+int cc_tuning_default(cc_tuning* out) {
+  if (!out) return CC_ERR_INVALID_ARG;
+  *out = public_default_tuning();
+  return CC_OK;
+}
+
+int cc_graph_set_tuning(cc_graph* g, const cc_tuning* t) {
+  if (!g || !t || !tuning_valid(*t)) return CC_ERR_INVALID_ARG;
+  g->tune = device_tuning(*t);
+  return CC_OK;
+}
+
+int cc_graph_get_tuning(const cc_graph* g, cc_tuning* out) {
+  if (!g || !out) return CC_ERR_INVALID_ARG;
+  const cc_tuning b = batch_tuning();
+  *out = b;
+  out->walk_batches = g->tune.walk_batches;
+  out->prefetch_ahead = g->tune.prefetch_ahead;
+  out->inline_heavy = g->tune.inline_heavy;
+  out->inline_decide = g->tune.inline_decide;
+  out->inline_rebuild = g->tune.inline_rebuild;
+  out->heavy_shift = g->tune.heavy_shift;
+  return CC_OK;
+}
+
+int cc_set_batch_tuning(const cc_tuning* t) {
+  if (!t || !tuning_valid(*t)) return CC_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_batch_tuning = *t;
+  g_batch_tuning_set = true;
+  return CC_OK;
+}
+
+int cc_get_batch_tuning(cc_tuning* out) {
+  if (!out) return CC_ERR_INVALID_ARG;
+  *out = batch_tuning();
+  return CC_OK;
+}
 
 int cc_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, const uint64_t* seeds, int32_t k_perms,
                   int64_t* D_out, int32_t* rounds_out) {

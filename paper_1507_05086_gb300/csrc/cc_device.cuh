@@ -163,6 +163,14 @@ constexpr int kLbsW = 32 * kLbsK;
 #endif
 constexpr int kLbsBatches = CC_LBS_BATCHES;   // batches per chunk of a long walk
 
+// Run-time shape of a walk (the defaults above unless a tuning says
+// otherwise): batches per chunk (1..8) and batches of a long row prefetched
+// ahead (0..8).  Neither changes what a walk visits, only its schedule.
+struct WalkShape {
+  int batches = kLbsBatches;
+  int pf_ahead = kLbsPfAhead;
+};
+
 struct LbsWarp {
   int32_t mark[kLbsW];   // relative item index per position
   int32_t rel[kLbsW];    // item start relative to the batch base
@@ -230,7 +238,7 @@ template <class F>
 __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, int64_t c0, int64_t cend, LbsWarp* ws,
                                           F& f, const int64_t* delta, const int32_t* vtx,
                                           const uint32_t* vmap = nullptr, uint32_t vsub = 0,
-                                          const int32_t* colp = nullptr, int64_t E = 0) {
+                                          const int32_t* colp = nullptr, int64_t E = 0, int pf_ahead = kLbsPfAhead) {
   const int lane = threadIdx.x & 31;
   int64_t j0 = warp_upper_bound(epos, nitems, c0) - 1;
   // cached item (warp-uniform): valid when cur_j == j0
@@ -255,8 +263,8 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
         L.ri[t] = 0;
         if (base + lane + 32 * t < cend) L.valid |= 1u << t;
       }
-      if (colp && lane < kLbsW / 32) {
-        const int64_t pe = base + (int64_t)kLbsPfAhead * kLbsW + 32 * lane;
+      if (colp && pf_ahead > 0 && lane < kLbsW / 32) {
+        const int64_t pe = base + (int64_t)pf_ahead * kLbsW + 32 * lane;
         if (pe < cur_end && pe < E) prefetch_l2(colp + pe + cur_dlt);
       }
       f(L);
@@ -355,7 +363,7 @@ __device__ __forceinline__ void lbs_chunk(const int64_t* epos, int64_t nitems, i
       cur_vtx = vtx ? ws->vtx[m] : 0;
       // the next batches of that item: start streaming them
       if (colp) {
-        for (int a = 1; a <= kLbsPfAhead; ++a) {
+        for (int a = 1; a <= pf_ahead; ++a) {
           const int64_t pe = base + (int64_t)a * kLbsW + 32 * lane;
           if (lane < kLbsW / 32 && pe >= cur_start && pe < cur_end && pe < E) prefetch_l2(colp + pe + cur_dlt);
         }
@@ -375,15 +383,16 @@ __device__ __forceinline__ void lbs_for_each_in(int64_t gwarp, int64_t nwarps, c
                                                 int64_t E, LbsWarp* ws, F&& f, const int64_t* delta = nullptr,
                                                 const int32_t* vtx = nullptr, int64_t E0 = 0,
                                                 const uint32_t* vmap = nullptr, uint32_t vsub = 0,
-                                                const int32_t* colp = nullptr) {
+                                                const int32_t* colp = nullptr, WalkShape shape = WalkShape{}) {
   if (E <= E0) return;
-  // up to kLbsBatches batches per chunk, fewer when the list is short, so
+  // up to shape.batches batches per chunk, fewer when the list is short, so
   // that short lists still spread over many warps
   int64_t nb = (E - E0) / (nwarps * (int64_t)kLbsW * 2);
-  nb = nb < 1 ? 1 : (nb > kLbsBatches ? kLbsBatches : nb);
+  nb = nb < 1 ? 1 : (nb > shape.batches ? shape.batches : nb);
   const int64_t kChunk = (int64_t)kLbsW * nb;
   for (int64_t c0 = E0 + gwarp * kChunk; c0 < E; c0 += nwarps * kChunk)
-    lbs_chunk(epos, nitems, c0, c0 + kChunk < E ? c0 + kChunk : E, ws, f, delta, vtx, vmap, vsub, colp, E);
+    lbs_chunk(epos, nitems, c0, c0 + kChunk < E ? c0 + kChunk : E, ws, f, delta, vtx, vmap, vsub, colp, E,
+              shape.pf_ahead);
 }
 
 template <class F>

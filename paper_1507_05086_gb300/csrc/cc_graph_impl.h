@@ -31,6 +31,7 @@ struct cc_graph {
   void* round_ws = nullptr;
   size_t round_ws_bytes = 0;
   int grid = 0;
+  ccg::Tuning tune = ccg::default_tuning();   // schedule settings of this graph's clusterings
   int async_grid = 0;            // co-resident grid of the asynchronous C4 decisions
   int32_t withhold = 0;          // test hook for the next clustering (cc_debug_withhold_release)
   int32_t* labels_tmp = nullptr;

@@ -75,6 +75,21 @@ struct Ctl {
   unsigned long long ph_ns[8];
 };
 
+// Schedule settings of the round kernel (the device side of cc_tuning in
+// include/cc.h).  None of them changes a result, only how the work is cut.
+struct Tuning {
+  int32_t walk_batches;      // edge walker: 128-entry batches per warp chunk
+  int32_t prefetch_ahead;    // edge walker: batches of a long row prefetched into L2
+  int32_t inline_heavy;      // heavy lists up to this long are scanned by the coordinator block
+  int32_t inline_decide;     // C4 blocked lists up to this long are decided inside the barrier
+  int32_t inline_rebuild;    // degree-order segments up to this long are read by the coordinator
+  int32_t heavy_shift;       // heavy-list threshold tau = max(1, D >> heavy_shift)
+};
+Tuning default_tuning();
+// Process-wide settings of batched jobs (cc_set_batch_tuning): the size
+// classes and the round-kernel settings of their jobs.
+Tuning batch_settings(int64_t* small_n, int64_t* team_n, int* team_blocks);
+
 struct RoundBuffers {
   int64_t n, nnz;
   int32_t max_deg;
@@ -118,6 +133,7 @@ struct RoundBuffers {
   RoundStat* stats;
   int64_t stats_cap;
   Ctl* ctl;
+  Tuning tune;
   // batched jobs only: writable order, permutation scratch
   int32_t* order_w;
   int32_t* ptmp;

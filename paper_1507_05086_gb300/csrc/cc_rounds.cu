@@ -58,9 +58,11 @@ constexpr int kScanU = 4;                    // list entries per thread per scan
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
 constexpr int kRun = 0, kDone = 1, kAbort = 3, kRebuildDelta = 4, kScanH = 5, kDrawBatch = 6;
 constexpr int kRebuildDeg = 7, kRebuildHeavy = 8;   // Delta search over the degree order, heavy refill
-constexpr int64_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
-constexpr int64_t kInlineDecide = 4096;      // C4 blocked lists up to this size are decided by the coordinator
-constexpr int64_t kInlineRebuild = 8192;     // heavy-list rebuilds over prefixes up to this size run in the coordinator
+// Defaults of the run-time schedule settings (Tuning; cc_tuning in the C ABI)
+constexpr int32_t kInlineH = 8192;           // heavy lists up to this size are scanned by the coordinator
+constexpr int32_t kInlineDecide = 4096;      // C4 blocked lists up to this size are decided by the coordinator
+constexpr int32_t kInlineRebuild = 8192;     // heavy-list rebuilds over prefixes up to this size run in the coordinator
+constexpr int32_t kHeavyShift = 1;           // heavy-list threshold tau = max(1, D >> kHeavyShift)
 
 // State word of a vertex (uint32):
 //   alive ........... kAlive | residual degree
@@ -215,10 +217,16 @@ struct K {
     // w * G + b), so a short walk spreads over every SM instead of the
     // first few blocks.
     lbs_for_each_in((int64_t)(threadIdx.x >> 5) * G + bid, ((int64_t)G * blockDim.x) >> 5, epos, nitems,
-                    E, lbs_ws(), f, delta, vtx, 0, vmap, vsub, delta ? B.col : nullptr);
+                    E, lbs_ws(), f, delta, vtx, 0, vmap, vsub, delta ? B.col : nullptr,
+                    WalkShape{B.tune.walk_batches, B.tune.prefetch_ahead});
   }
 
   __device__ __forceinline__ const Plan& P() const { return S->plan; }
+  // heavy-list threshold for a maximum degree D
+  __device__ __forceinline__ int32_t tau_of(int32_t D) const {
+    const int32_t t = D >> B.tune.heavy_shift;
+    return t >= 1 ? t : 1;
+  }
   __device__ __forceinline__ Coord& co() const { return S->co; }
   __device__ void fail(int code) { atomicCAS(&C->err, kOk, code); }
 
@@ -451,7 +459,7 @@ struct K {
         dec = 2;                          // every alive vertex is isolated: Delta = 0
       } else if (c.h_len == 0) {
         dec = 3;                          // no heavy list yet: build it
-      } else if (c.h_len > kInlineH) {
+      } else if (c.h_len > B.tune.inline_heavy) {
         p.state = kScanH; p.win_lo = 0; p.win_len = c.h_len;
       } else {
         dec = 0;                          // scan the short heavy list here
@@ -508,7 +516,7 @@ struct K {
   // degree seen is D exactly if it is >= t (no unread vertex can reach t);
   // otherwise t halves and the next segment is read.  The heavy list then
   // comes from the prefix of full degree >= D/2.  Segments up to
-  // kInlineRebuild vertices are read by the coordinator block inside the
+  // inline_rebuild vertices (a tuning setting) are read by the coordinator block inside the
   // barrier; longer ones by the grid.  Once the prefix to read exceeds a
   // quarter of the compact list of alive non-isolated vertices (vertex order,
   // dead vertices dropped at each of its rebuilds), that list is cheaper and
@@ -539,14 +547,14 @@ struct K {
         const int64_t seg = c.rb_hi - c.rb_lo;
         int dec;
         if (seg > 0) {
-          dec = seg <= kInlineRebuild ? 0 : (c.rb_hi > limit ? 4 : 1);
+          dec = seg <= B.tune.inline_rebuild ? 0 : (c.rb_hi > limit ? 4 : 1);
         } else if (c.rb_D >= c.rb_t || c.rb_t <= 1) {
           if (c.rb_D <= 0) {
             dec = 5;                                  // nothing alive has an alive neighbour
           } else {
-            c.tau = c.rb_D >= 2 ? c.rb_D >> 1 : 1;
+            c.tau = tau_of(c.rb_D);
             c.rb_hi = __ldg(B.dge + c.tau);           // heavy candidates: full degree >= tau
-            dec = c.rb_hi <= kInlineRebuild ? 2 : (c.rb_hi > limit ? 4 : 3);
+            dec = c.rb_hi <= B.tune.inline_rebuild ? 2 : (c.rb_hi > limit ? 4 : 3);
           }
         } else {
           c.rb_t = c.rb_t >= 2 ? c.rb_t >> 1 : 1;
@@ -631,7 +639,7 @@ struct K {
   __device__ void finish_rebuild(int32_t D, int64_t hcount) {
     if (threadIdx.x == 0) {
       Coord& c = co();
-      c.tau = D >= 2 ? D >> 1 : 1;
+      c.tau = tau_of(D);
       c.h_len = D > 0 ? hcount : 0;
       if (D <= 0) c.delta_zero = 1;
     }
@@ -779,7 +787,7 @@ struct K {
             Coord& c = co();
             c.nz_total = tot;
             c.d_new = (int32_t)(D > 0 ? D : 0);
-            S->plan.th = D >= 2 ? (int32_t)(D >> 1) : 1;
+            S->plan.th = tau_of((int32_t)D);
             C->h_pack = 0;
           }
         }))
@@ -1471,7 +1479,7 @@ __device__ void run_job(K& k, int algo) {
           };
           while (S.plan.undecided > 0) {
             k.c4_fix_scan();
-            if (S.plan.b_n <= kInlineDecide) {
+            if (S.plan.b_n <= k.B.tune.inline_decide) {
               // a short blocked list: the coordinator decides inside the barrier
               if (!k.sync(5, [&] {
                     const long long left = block_sum<int64_t>(k.c4_fix_decide(threadIdx.x, blockDim.x), S.scr);
@@ -1800,6 +1808,10 @@ __global__ void k_finalize_labels(RoundBuffers B, int32_t* __restrict__ labels) 
 
 }  // namespace
 
+Tuning default_tuning() {
+  return Tuning{kLbsBatches, kLbsPfAhead, kInlineH, kInlineDecide, kInlineRebuild, kHeavyShift};
+}
+
 size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   const size_t nn = (size_t)(n > 0 ? n : 1);
   size_t b = 0;
@@ -1820,6 +1832,7 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
 
 void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* B) {
   const size_t nn = (size_t)(n > 0 ? n : 1);
+  B->tune = default_tuning();
   char* p = static_cast<char*>(ws);
   auto take = [&](size_t bytes) { char* q = p; p += align_up(bytes); return q; };
   B->ctl = reinterpret_cast<Ctl*>(take(sizeof(Ctl)));

@@ -5,8 +5,9 @@
 // of cc_rounds.cu (a whole job -- permutation, rounds, objective, labels --
 // inside one launch) and never waits for the GPU:
 //
-//   * small graphs (n <= kServeSmallN): one thread block per job, batched;
-//   * medium graphs (n <= kServeTeamN): one team of kServeTeamBlocks blocks
+//   * small graphs (n <= batch_small_n of the batch settings, 2^16 by
+//     default): one thread block per job, batched;
+//   * medium graphs (n <= batch_team_n, 2^21): one team of batch_team_blocks
 //     per job, batched in cooperative launches of at most kServeTeamMax teams,
 //     kServeTeamFlights such launches in flight at a time (together at most
 //     two thirds of the batched kernel's co-resident blocks, so that small
@@ -44,9 +45,6 @@ using namespace ccg;
 
 namespace {
 
-constexpr int64_t kServeSmallN = 1 << 16;    // one thread block per job up to this size
-constexpr int64_t kServeTeamN = 1 << 21;     // one team of blocks per job up to this size
-constexpr int kServeTeamBlocks = 8;
 constexpr int kServeTeamMax = 16;            // teams per cooperative launch, at most
 constexpr int kServeTeamFlights = 2;         // medium launches in flight at once
 constexpr int kStreams = 16;             // launches in flight at once (one stream each)
@@ -54,8 +52,6 @@ constexpr int kStreams = 16;             // launches in flight at once (one stre
 using Clock = std::chrono::steady_clock;
 
 enum Cls { kSmall = 0, kTeam = 1, kWhole = 2 };
-
-int class_of(int64_t n) { return n <= kServeSmallN ? kSmall : (n <= kServeTeamN ? kTeam : kWhole); }
 
 struct Request {
   int64_t ticket;
@@ -102,6 +98,11 @@ struct cc_server {
   size_t in_use = 0;
   int max_batch = 0;
   int grid = 0;                  // co-resident blocks of the batched kernel
+  // size classes and round settings (the batch settings when created):
+  // one block per job up to small_n vertices, a team of team_blocks up to team_n
+  int64_t small_n = 0, team_n = 0;
+  int team_blocks = 0;
+  Tuning tune;
   std::mutex mu;
   std::condition_variable cv_work, cv_done, cv_whole;
   std::deque<Request> pending;   // small and medium requests, in arrival order
@@ -123,18 +124,20 @@ int cuda_status(cudaError_t e) {
   return e == cudaErrorMemoryAllocation ? CC_ERR_OOM : CC_ERR_CUDA;
 }
 
-int team_of(int cls) { return cls == kSmall ? 1 : kServeTeamBlocks; }
+int class_of(const cc_server* sv, int64_t n) { return n <= sv->small_n ? kSmall : (n <= sv->team_n ? kTeam : kWhole); }
+
+int team_of(const cc_server* sv, int cls) { return cls == kSmall ? 1 : sv->team_blocks; }
 
 // Teams of one launch: every job gets one while the launch stays co-resident
 // (small: the batched kernel's whole grid; medium: kServeTeamMax teams).
 int teams_for(const cc_server* sv, int cls, size_t jobs) {
   const int cap = cls == kSmall ? sv->grid
-                                 : std::min(kServeTeamMax, sv->grid / kServeTeamBlocks / (kServeTeamFlights + 1));
+                                 : std::min(kServeTeamMax, sv->grid / sv->team_blocks / (kServeTeamFlights + 1));
   return (int)std::min<size_t>(jobs, (size_t)std::max(cap, 1));
 }
 
 size_t batch_bytes(const cc_server* sv, int cls, int64_t n_max, size_t jobs) {
-  return align_up(batch_slot_bytes(n_max, team_of(cls))) * (size_t)teams_for(sv, cls, jobs);
+  return align_up(batch_slot_bytes(n_max, team_of(sv, cls))) * (size_t)teams_for(sv, cls, jobs);
 }
 
 // Pinned host staging of a flight, grown when a batch needs more.
@@ -180,7 +183,7 @@ int start_batch(cc_server* sv, Flight& f, int cls, std::vector<Request>& reqs) {
                         })->g->n;
   const int algo = reqs[0].algo;
   const int64_t ppm = reqs[0].eps_ppm;
-  const int team = team_of(cls);
+  const int team = team_of(sv, cls);
   const int teams = teams_for(sv, cls, reqs.size());
   const size_t slot = align_up(batch_slot_bytes(n_max, team));
   int rc = ensure_host(f, reqs.size(), (size_t)teams);
@@ -192,6 +195,7 @@ int start_batch(cc_server* sv, Flight& f, int cls, std::vector<Request>& reqs) {
     e = pool_malloc(reinterpret_cast<void**>(&f.slots_dev), sizeof(RoundBuffers) * (size_t)teams, f.stream);
   for (int t = 0; t < teams && e == cudaSuccess; ++t) {
     batch_slot_carve(static_cast<char*>(f.ws) + slot * (size_t)t, n_max, team, &f.slots_host[t]);
+    f.slots_host[t].tune = sv->tune;
     e = cudaMemsetAsync(f.slots_host[t].ctl, 0, sizeof(Ctl), f.stream);
   }
   if (e != cudaSuccess) {
@@ -302,7 +306,7 @@ bool gather(cc_server* sv, int cls, bool any_busy, std::vector<Request>& batch, 
   *need = 0;
   int64_t n_max = 0;
   for (auto it = sv->pending.begin(); it != sv->pending.end() && (int)batch.size() < sv->max_batch;) {
-    if (class_of(it->g->n) != cls ||
+    if (class_of(sv, it->g->n) != cls ||
         (!batch.empty() && (it->algo != batch.front().algo || it->eps_ppm != batch.front().eps_ppm))) {
       ++it;
       continue;
@@ -396,6 +400,7 @@ int cc_server_create(size_t mem_budget, int32_t max_batch, cc_server** out) {
   sv->budget = mem_budget;
   sv->max_batch = max_batch;
   sv->grid = batch_grid_size(sv->device);
+  sv->tune = batch_settings(&sv->small_n, &sv->team_n, &sv->team_blocks);
   for (auto& f : sv->fl) {
     if (cudaStreamCreateWithFlags(&f.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming) != cudaSuccess) {
@@ -454,7 +459,7 @@ int cc_server_submit(cc_server* sv, cc_graph* g, int algo, double eps, uint64_t 
   r.t_submit = Clock::now();
   sv->results[r.ticket] = Result{};
   *ticket = r.ticket;
-  if (class_of(g->n) == kWhole) {
+  if (class_of(sv, g->n) == kWhole) {
     sv->whole.push_back(r);
     sv->cv_whole.notify_one();
   } else {

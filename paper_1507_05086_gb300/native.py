@@ -40,6 +40,28 @@ class RoundStats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ROUND_STAT_FIELDS]
 
 
+TUNING_FIELDS = (("walk_batches", ctypes.c_int32), ("prefetch_ahead", ctypes.c_int32),
+                 ("inline_heavy", ctypes.c_int32), ("inline_decide", ctypes.c_int32),
+                 ("inline_rebuild", ctypes.c_int32), ("heavy_shift", ctypes.c_int32),
+                 ("batch_small_n", ctypes.c_int64), ("batch_team_n", ctypes.c_int64),
+                 ("batch_team_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32))
+
+
+class Tuning(ctypes.Structure):
+    """cc_tuning: schedule settings, none of which changes a result."""
+    _fields_ = list(TUNING_FIELDS)
+
+    def to_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in TUNING_FIELDS if f != "reserved"}
+
+    @classmethod
+    def from_dict(cls, d):
+        t = default_tuning()
+        for k, v in d.items():
+            setattr(t, k, int(v))
+        return t
+
+
 class CCError(RuntimeError):
     def __init__(self, fn: str, status: int):
         super().__init__(f"{fn} failed: {STATUS.get(status, 'unknown')} ({status})")
@@ -109,6 +131,12 @@ def load(build_if_missing: bool = True):
         lib.cc_server_device_times.argtypes = [vp, i64, vp, vp]
         lib.cc_server_destroy.restype = ci
         lib.cc_server_destroy.argtypes = [vp]
+        for f in ("cc_tuning_default", "cc_get_batch_tuning", "cc_set_batch_tuning"):
+            getattr(lib, f).restype = ci
+            getattr(lib, f).argtypes = [vp]
+        for f in ("cc_graph_set_tuning", "cc_graph_get_tuning"):
+            getattr(lib, f).restype = ci
+            getattr(lib, f).argtypes = [vp, vp]
         lib.cc_batch_run.restype = ci
         lib.cc_batch_run.argtypes = [vp, i32, ci, ctypes.c_double, vp, i32, vp, vp, vp, vp]
         _lib = lib
@@ -222,6 +250,17 @@ class Graph:
                                                   ctypes.byref(rounds), ctypes.byref(d)))
         return labels_out, rounds.value, d.value
 
+    def set_tuning(self, tuning):
+        """Schedule settings of this graph's clusterings (a Tuning or a dict of
+        its fields; missing fields keep their defaults)."""
+        t = tuning if isinstance(tuning, Tuning) else Tuning.from_dict(tuning)
+        _check("cc_graph_set_tuning", self._lib.cc_graph_set_tuning(self._h, ctypes.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check("cc_graph_get_tuning", self._lib.cc_graph_get_tuning(self._h, ctypes.byref(t)))
+        return t.to_dict()
+
     def set_timing(self, enable: bool = True):
         _check("cc_graph_set_timing", self._lib.cc_graph_set_timing(self._h, 1 if enable else 0))
 
@@ -252,6 +291,24 @@ class Graph:
         d = ctypes.c_int64()
         _check("cc_disagreements", self._lib.cc_disagreements(self._h, _ptr(labels), ctypes.byref(d)))
         return d.value
+
+
+def default_tuning() -> Tuning:
+    t = Tuning()
+    _check("cc_tuning_default", load().cc_tuning_default(ctypes.byref(t)))
+    return t
+
+
+def set_batch_tuning(tuning):
+    """Process-wide settings of batched jobs and servers created later."""
+    t = tuning if isinstance(tuning, Tuning) else Tuning.from_dict(tuning)
+    _check("cc_set_batch_tuning", load().cc_set_batch_tuning(ctypes.byref(t)))
+
+
+def get_batch_tuning() -> dict:
+    t = Tuning()
+    _check("cc_get_batch_tuning", load().cc_get_batch_tuning(ctypes.byref(t)))
+    return t.to_dict()
 
 
 def release_memory():
