@@ -156,14 +156,14 @@ def measured_hbm_peak():
 
 # DRAM traffic of the round kernel per algorithmic byte, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum, a one-pass metric set, of the
-# second k_rounds launch of a run on the default workload, R-MAT scale 26,
-# eps 0.5: ClusterWild! 53.13 GB against 18.19 GB algorithmic, C4 53.32 GB
-# against 18.80 GB), keyed by a digest of the kernel's code (comments and
-# blank lines left out): a changed kernel reports traffic null until it is
-# captured again.
+# two timed k_rounds launches of `bench.py --steps 1 --warmup 1` on the
+# default workload, R-MAT scale 26, eps 0.5: ClusterWild! 46.34 GB against
+# 18.19 GB algorithmic, C4 46.64 GB against 18.80 GB), keyed by a digest of the
+# kernel's code (comments and blank lines left out): a changed kernel reports
+# traffic null until it is captured again.
 ROUNDS_SOURCES = ("paper_1507_05086_gb300/csrc/cc_rounds.cu", "paper_1507_05086_gb300/csrc/cc_device.cuh",
                   "paper_1507_05086_gb300/csrc/cc_internal.h")
-ROUNDS_TRAFFIC_PER_BYTE = {"ad6899ca79fc6d64": (53.13e9 + 53.32e9) / (18.19e9 + 18.80e9)}
+ROUNDS_TRAFFIC_PER_BYTE = {"42571330206c9fbb": (46.34e9 + 46.64e9) / (18.19e9 + 18.80e9)}
 
 
 def rounds_sources_digest() -> str:

@@ -94,6 +94,11 @@ extern "C" {
 #define CC_DEVICE_PTRS  2u   /* row_offsets/col_idx are device pointers, adopted by
                                 reference (caller keeps them alive until destroy) */
 #define CC_OFFSETS_I32  4u   /* row_offsets is int32[n+1] instead of int64[n+1]  */
+#define CC_VALIDATE_EXACT 8u /* check symmetry exactly: every entry (u, w) with u < w is
+                                looked up in row w by binary search (slower: about 10
+                                random reads per entry); without it symmetry is checked by
+                                two order-independent 64-bit hash sums of the pairs seen
+                                from either end, which a crafted graph could defeat */
 
 /* Limits: 0 <= n <= 2^31 - 32 (a 32-bit state word per vertex), nnz < 2^33. */
 
@@ -120,8 +125,8 @@ typedef struct cc_round_stats {
  *   col_idx      int32[off[n]]: each row strictly increasing, no self loop,
  *                every entry in [0,n), and the graph symmetric (u in row v iff
  *                v in row u).  Isolated vertices are allowed.
- *   flags        CC_VALIDATE / CC_DEVICE_PTRS / CC_OFFSETS_I32 (any other bit:
- *                CC_ERR_INVALID_ARG).
+ *   flags        CC_VALIDATE / CC_DEVICE_PTRS / CC_OFFSETS_I32 / CC_VALIDATE_EXACT
+ *                (any other bit: CC_ERR_INVALID_ARG).
  *   cuda_stream  cudaStream_t for all work on this graph (NULL = legacy stream).
  *   out          receives the handle.
  * Host arrays are copied; the caller may free them on return.  The CSR is

@@ -246,7 +246,7 @@ int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, 
   if (!out) return CC_ERR_INVALID_ARG;
   *out = nullptr;
   if (n < 0 || n > 2147483616LL || !row_offsets) return CC_ERR_INVALID_ARG;
-  if (flags & ~(CC_VALIDATE | CC_DEVICE_PTRS | CC_OFFSETS_I32)) return CC_ERR_INVALID_ARG;
+  if (flags & ~(CC_VALIDATE | CC_DEVICE_PTRS | CC_OFFSETS_I32 | CC_VALIDATE_EXACT)) return CC_ERR_INVALID_ARG;
   const bool dev = (flags & CC_DEVICE_PTRS) != 0, i32 = (flags & CC_OFFSETS_I32) != 0;
   cc_graph* g = new (std::nothrow) cc_graph();
   if (!g) return CC_ERR_OOM;
@@ -354,6 +354,8 @@ int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, 
       launch_validate_edges(n, cut[c], cut[c + 1], c == chunks - 1, g->nz_row, g->nz_pos, g->nz_n, g->col, vws,
                             g->num_sms, s);
     }
+    if (flags & CC_VALIDATE_EXACT)
+      launch_validate_reverse(nnz, g->off, g->nz_row, g->nz_pos, g->nz_n, g->col, vws, g->num_sms, s);
     cudaMemcpyAsync(vflags, vflags_dev, sizeof(vflags), cudaMemcpyDeviceToHost, s);
     dfree(vws, s);
     dfree(nws, s);

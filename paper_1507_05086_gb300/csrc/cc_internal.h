@@ -199,6 +199,10 @@ cudaError_t launch_validate_offsets(int64_t n, int64_t nnz, const int64_t* off, 
 cudaError_t launch_validate_edges(int64_t n, int64_t e0, int64_t e1, bool last, const int32_t* nz_row,
                                   const int64_t* nz_pos, int64_t nz_n, const int32_t* col, void* ws, int num_sms,
                                   cudaStream_t stream);
+// Exact symmetry check (CC_VALIDATE_EXACT): reverse-entry search for every
+// lower entry; shares ws (and its error word) with the validation above.
+cudaError_t launch_validate_reverse(int64_t nnz, const int64_t* off, const int32_t* nz_row, const int64_t* nz_pos,
+                                    int64_t nz_n, const int32_t* col, void* ws, int num_sms, cudaStream_t stream);
 cudaError_t launch_offsets_i32_to_i64(int64_t n, const int32_t* in, int64_t* out, cudaStream_t stream);
 // dsort (int32[nz_n]): the non-isolated vertices, largest degree first;
 // dge (int64[max_deg + 2]): dge[t] = number of vertices of degree >= t.

@@ -122,6 +122,35 @@ __global__ void __launch_bounds__(kValThreads) k_validate_edges(int64_t n, int64
   }
 }
 
+// Exact symmetry (opt-in): every entry (u, w) with u < w must have u in row w,
+// found by binary search in that sorted row.  Together with the equal counts
+// of lower and upper entries (k_validate_symmetry) this makes the entries
+// seen from the two ends the same set of pairs.
+__global__ void __launch_bounds__(kValThreads) k_validate_reverse(int64_t nz_n, const int32_t* __restrict__ nz_row,
+                                                                 const int64_t* __restrict__ nz_pos, int64_t nnz,
+                                                                 const int64_t* __restrict__ off,
+                                                                 const int32_t* __restrict__ col, int* flags) {
+  __shared__ LbsWarp lbs[kValThreads / 32];
+  int bad = 0;
+  lbs_for_each(nz_pos, nz_n, nnz, &lbs[threadIdx.x >> 5], [&](const Lbs& L) {
+#pragma unroll
+    for (int t = 0; t < kLbsK; ++t) {
+      if (!L.ok(t)) continue;
+      const int32_t u = __ldg(nz_row + L.item(t));
+      const int32_t w = __ldg(col + L.edge(t));
+      if (w <= u) continue;
+      int64_t lo = __ldg(off + w), hi = __ldg(off + w + 1);
+      while (lo < hi) {
+        const int64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(col + mid) < u) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= __ldg(off + w + 1) || __ldg(col + lo) != u) bad = kAsymmetric;
+    }
+  }, nullptr, nullptr, 0, col);
+  if (bad) atomicCAS(flags, 0, bad);
+}
+
 __global__ void k_validate_finish(int64_t n, const int64_t* __restrict__ off, int64_t nnz, int* flags,
                                   const unsigned long long* sums) {
   (void)sums;
@@ -209,23 +238,44 @@ __global__ void __launch_bounds__(kDegThreads) k_deg_hist(int64_t nz_n, const in
     if (bin[b]) atomicAdd(cnt + b, (unsigned long long)bin[b]);
 }
 
-// One block: dge[t] = sum of cnt[d] over d >= t (suffix sums, top down), then
-// cnt[d] becomes the first position of degree d in dsort, dge[d + 1].
-__global__ void __launch_bounds__(kDegThreads) k_deg_suffix(int64_t max_deg, unsigned long long* __restrict__ cnt,
-                                                           int64_t* __restrict__ dge) {
+// dge[t] = sum of cnt[d] over d >= t (suffix sums), in three steps over tiles
+// of kDegThreads entries: each tile's own suffix sums and total, a suffix
+// scan of the tile totals by one block, then each entry adds the totals of
+// the tiles after its own.  cnt[d] then becomes the first position of degree
+// d in dsort, dge[d + 1] = dge[d] - cnt[d].
+__global__ void __launch_bounds__(kDegThreads) k_deg_suffix_tiles(int64_t len, const unsigned long long* __restrict__ cnt,
+                                                                 int64_t* __restrict__ dge, int64_t* __restrict__ tile_tot) {
   __shared__ int64_t scr[33];
-  const int64_t len = max_deg + 2;              // indices 0 .. max_deg + 1
+  // tile t covers indices [len - (t + 1) * kDegThreads, len - t * kDegThreads), read top down
+  const int64_t idx = len - 1 - ((int64_t)blockIdx.x * kDegThreads + threadIdx.x);
+  const int64_t x = idx >= 0 ? (int64_t)cnt[idx] : 0;
+  int64_t tot;
+  const int64_t ex = block_exclusive_sum<int64_t>(x, scr, &tot);
+  if (idx >= 0) dge[idx] = ex + x;
+  if (threadIdx.x == 0) tile_tot[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kDegThreads) k_deg_suffix_totals(int64_t ntiles, int64_t* __restrict__ tile_tot) {
+  __shared__ int64_t scr[33];
   int64_t run = 0;
-  for (int64_t base = 0; base < len; base += blockDim.x) {
-    const int64_t idx = len - 1 - (base + threadIdx.x);
-    const int64_t x = idx >= 0 ? (int64_t)cnt[idx] : 0;
+  for (int64_t base = 0; base < ntiles; base += blockDim.x) {
+    const int64_t t = base + threadIdx.x;
+    const int64_t x = t < ntiles ? tile_tot[t] : 0;
     int64_t tot;
     const int64_t ex = block_exclusive_sum<int64_t>(x, scr, &tot);
-    if (idx >= 0) dge[idx] = run + ex + x;
+    if (t < ntiles) tile_tot[t] = run + ex;     // the totals of the tiles above tile t
     run += tot;
   }
-  __syncthreads();
-  for (int64_t d = threadIdx.x; d <= max_deg; d += blockDim.x) cnt[d] = (unsigned long long)dge[d + 1];
+}
+
+__global__ void __launch_bounds__(kDegThreads) k_deg_suffix_add(int64_t len, unsigned long long* __restrict__ cnt,
+                                                               int64_t* __restrict__ dge,
+                                                               const int64_t* __restrict__ tile_tot) {
+  const int64_t idx = len - 1 - ((int64_t)blockIdx.x * kDegThreads + threadIdx.x);
+  if (idx < 0) return;
+  const int64_t d = dge[idx] + tile_tot[blockIdx.x];
+  dge[idx] = d;
+  if (idx < len - 1) cnt[idx] = (unsigned long long)(d - (int64_t)cnt[idx]);
 }
 
 __global__ void __launch_bounds__(kDegThreads) k_deg_scatter(int64_t nz_n, const int32_t* __restrict__ nz_row,
@@ -264,16 +314,24 @@ __global__ void __launch_bounds__(kDegThreads) k_deg_scatter(int64_t nz_n, const
 
 }  // namespace
 
-size_t degree_order_workspace_bytes(int32_t max_deg) { return align_up(8 * ((size_t)max_deg + 2)); }
+size_t degree_order_workspace_bytes(int32_t max_deg) {
+  const size_t len = (size_t)max_deg + 2;
+  return align_up(8 * len) + align_up(8 * ((len + kDegThreads - 1) / kDegThreads));
+}
 
 cudaError_t launch_degree_order(int64_t nz_n, const int32_t* nz_row, const int64_t* off, int32_t max_deg,
                                 int32_t* dsort, int64_t* dge, void* ws, int num_sms, cudaStream_t stream) {
+  const int64_t len = (int64_t)max_deg + 2;             // degrees 0 .. max_deg + 1
+  const int64_t ntiles = (len + kDegThreads - 1) / kDegThreads;
   unsigned long long* cnt = static_cast<unsigned long long*>(ws);
-  cudaError_t e = cudaMemsetAsync(cnt, 0, degree_order_workspace_bytes(max_deg), stream);
+  int64_t* tile_tot = reinterpret_cast<int64_t*>(static_cast<char*>(ws) + align_up(8 * (size_t)len));
+  cudaError_t e = cudaMemsetAsync(cnt, 0, 8 * (size_t)len, stream);
   if (e != cudaSuccess) return e;
   const int g = num_sms > 0 ? num_sms : 1;
   if (nz_n > 0) k_deg_hist<<<g, kDegThreads, 0, stream>>>(nz_n, nz_row, off, cnt);
-  k_deg_suffix<<<1, kDegThreads, 0, stream>>>(max_deg, cnt, dge);
+  k_deg_suffix_tiles<<<(unsigned)ntiles, kDegThreads, 0, stream>>>(len, cnt, dge, tile_tot);
+  k_deg_suffix_totals<<<1, kDegThreads, 0, stream>>>(ntiles, tile_tot);
+  k_deg_suffix_add<<<(unsigned)ntiles, kDegThreads, 0, stream>>>(len, cnt, dge, tile_tot);
   if (nz_n > 0) k_deg_scatter<<<g, kDegThreads, 0, stream>>>(nz_n, nz_row, off, cnt, dsort);
   return cudaGetLastError();
 }
@@ -320,6 +378,13 @@ cudaError_t launch_validate_edges(int64_t n, int64_t e0, int64_t e1, bool last, 
   if (e1 > e0)
     k_validate_edges<<<num_sms * 2, kValThreads, 0, stream>>>(n, e0, e1, nz_n, nz_row, nz_pos, col, flags, sums);
   if (last) k_validate_symmetry<<<1, 1, 0, stream>>>(flags, sums);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_reverse(int64_t nnz, const int64_t* off, const int32_t* nz_row, const int64_t* nz_pos,
+                                    int64_t nz_n, const int32_t* col, void* ws, int num_sms, cudaStream_t stream) {
+  int* flags = reinterpret_cast<int*>(static_cast<char*>(ws) + align_up(8 * sizeof(unsigned long long)));
+  if (nnz > 0) k_validate_reverse<<<num_sms * 2, kValThreads, 0, stream>>>(nz_n, nz_row, nz_pos, nnz, off, col, flags);
   return cudaGetLastError();
 }
 

@@ -27,6 +27,7 @@ ALGOS = {"c4": C4, "cw": CLUSTERWILD, "clusterwild": CLUSTERWILD, "c4-est": C4_E
 
 CC_DEVICE_PTRS = 2
 CC_OFFSETS_I32 = 4
+CC_VALIDATE_EXACT = 8
 
 STATUS = {
     0: "ok", -1: "invalid argument", -2: "invalid graph", -3: "out of memory", -4: "CUDA error",
@@ -179,11 +180,11 @@ class Graph:
     keep them alive).
     """
 
-    def __init__(self, off, col, stream=None):
+    def __init__(self, off, col, stream=None, exact_symmetry: bool = False):
         lib = load()
         self._lib = lib
         n = int(off.shape[0] - 1)
-        flags = 0
+        flags = CC_VALIDATE_EXACT if exact_symmetry else 0
         self._keep = None
         if _is_cuda(off) or _is_cuda(col):
             import torch

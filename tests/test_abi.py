@@ -46,12 +46,13 @@ def test_graph_create_rejects_unknown_flags_without_gpu():
     from paper_1507_05086_gb300 import native
     lib = native.load()
     flags = dict((k, int(v, 16) if v.startswith("0x") else int(v))
-                 for k, v in re.findall(r"#define\s+CC_(VALIDATE|DEVICE_PTRS|OFFSETS_I32)\s+(\w+?)u", open(HEADER).read()))
-    assert flags == {"VALIDATE": 1, "DEVICE_PTRS": 2, "OFFSETS_I32": 4}
+                 for k, v in re.findall(r"#define\s+CC_(VALIDATE|DEVICE_PTRS|OFFSETS_I32|VALIDATE_EXACT)\s+(\w+?)u",
+                                        open(HEADER).read()))
+    assert flags == {"VALIDATE": 1, "DEVICE_PTRS": 2, "OFFSETS_I32": 4, "VALIDATE_EXACT": 8}
     off = np.zeros(2, np.int64)
     h = ctypes.c_void_p()
     p = off.ctypes.data_as(ctypes.c_void_p)
-    assert lib.cc_graph_create(ctypes.c_int64(1), p, None, ctypes.c_uint32(8), None, ctypes.byref(h)) == -1
+    assert lib.cc_graph_create(ctypes.c_int64(1), p, None, ctypes.c_uint32(16), None, ctypes.byref(h)) == -1
     assert lib.cc_graph_create(ctypes.c_int64(-1), p, None, ctypes.c_uint32(1), None, ctypes.byref(h)) == -1
     assert not h.value
 

@@ -184,6 +184,15 @@ def test_device_pointers_and_determinism(cc, ora, gg):
             assert np.array_equal(lab, olab)
 
 
+def ora_free_disagreements(g, lab):
+    """Disagreements from the definition (numpy): cut positive edges plus
+    non-adjacent pairs inside clusters."""
+    src = np.repeat(np.arange(g.n), np.diff(g.off))
+    intra = int(np.sum(lab[src] == lab[g.col])) // 2
+    _, sizes = np.unique(lab, return_counts=True)
+    return g.m - intra + int(np.sum(sizes * (sizes - 1) // 2)) - intra
+
+
 def test_invalid_arguments_and_graphs(cc, gg):
     g = gg.rmat(8, 4, seed=0)
     with cc.Graph(g.off, g.col) as graph:
@@ -201,9 +210,23 @@ def test_invalid_arguments_and_graphs(cc, gg):
     bad.append((np.array([0, 1, 2], np.int64), np.array([1, 5], np.int32)))   # out of range
     bad.append((np.array([0, 2, 1], np.int64), np.array([1, 0], np.int32)))   # decreasing offsets
     for off, col in bad:
-        with pytest.raises(cc.CCError) as ei:
-            cc.Graph(off, col)
-        assert ei.value.status == -2
+        for exact in (False, True):
+            with pytest.raises(cc.CCError) as ei:
+                cc.Graph(off, col, exact_symmetry=exact)
+            assert ei.value.status == -2
+    # the exact symmetry check (reverse-entry search) accepts symmetric graphs
+    # with long rows and rejects a row whose entry has no reverse
+    g2 = gg.rmat(12, 8, seed=1)
+    assert int(np.diff(g2.off).max()) > 100
+    with cc.Graph(g2.off, g2.col, exact_symmetry=True) as gx:
+        lab, r, d = gx.cluster("cw", 0.5, 1)
+        assert r > 0 and d == ora_free_disagreements(g2, lab)
+    e = gg.from_edges(6, np.array([0, 1, 2], np.int32), np.array([3, 4, 5], np.int32))
+    ecol = e.col.copy()
+    ecol[int(e.off[3])] = 1            # row 3 lists 1 instead of 0
+    with pytest.raises(cc.CCError) as ei:
+        cc.Graph(e.off, ecol, exact_symmetry=True)
+    assert ei.value.status == -2
 
 
 def test_planted_partition_1m_all_eps(cc, ora, gg):
