@@ -335,8 +335,12 @@ int cc_server_destroy(cc_server* s);
  *   batch_team_n     one team of blocks per job up to this many vertices,
  *                    >= batch_small_n, <= 2^24 (2^21)
  *   batch_team_blocks  blocks per team, 2..16 (8)
+ *   warp_resolve_row C4: a round's blocked actives are decided one warp per
+ *                    vertex in one grid phase when each has a warp and no
+ *                    blocked row is longer than this (else by the fixpoint of
+ *                    synchronous passes), 0..2^24 (1024; 0 = always the fixpoint)
  * cc_tuning_default fills the defaults (in brackets).  cc_graph_set_tuning
- * sets the round-kernel settings (the first six) for the clusterings of one
+ * sets the round-kernel settings (all but the batch_* ones) for the clusterings of one
  * graph; cc_set_batch_tuning sets them, and the size classes, for every
  * later cc_batch_jobs / cc_batch_run call and every server created later
  * (process-wide).  Out-of-range values: CC_ERR_INVALID_ARG, nothing changed.
@@ -351,7 +355,7 @@ typedef struct cc_tuning {
   int64_t batch_small_n;
   int64_t batch_team_n;
   int32_t batch_team_blocks;
-  int32_t reserved;          /* 0 */
+  int32_t warp_resolve_row;
 } cc_tuning;
 int cc_tuning_default(cc_tuning* out);
 int cc_graph_set_tuning(cc_graph* g, const cc_tuning* t);

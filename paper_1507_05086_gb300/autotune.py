@@ -35,6 +35,7 @@ ROUND_KNOBS = {
     "inline_heavy": (2048, 8192, 32768),
     "inline_rebuild": (2048, 8192, 32768),
     "inline_decide": (1024, 4096, 16384),
+    "warp_resolve_row": (256, 1024, 4096),
 }
 BATCH_KNOBS = {
     "batch_team_blocks": (4, 8, 16),

@@ -85,7 +85,7 @@ cc_tuning public_default_tuning() {
   t.batch_small_n = kBatchSmallN;
   t.batch_team_n = kBatchTeamN;
   t.batch_team_blocks = kBatchTeamBlocks;
-  t.reserved = 0;
+  t.warp_resolve_row = d.warp_resolve_row;
   return t;
 }
 
@@ -94,11 +94,13 @@ bool tuning_valid(const cc_tuning& t) {
          t.inline_heavy >= 0 && t.inline_heavy <= 65536 && t.inline_decide >= 0 && t.inline_decide <= 65536 &&
          t.inline_rebuild >= 0 && t.inline_rebuild <= 65536 && t.heavy_shift >= 1 && t.heavy_shift <= 4 &&
          t.batch_small_n >= 1 && t.batch_small_n <= (1 << 20) && t.batch_team_n >= t.batch_small_n &&
-         t.batch_team_n <= (1 << 24) && t.batch_team_blocks >= 2 && t.batch_team_blocks <= 16 && t.reserved == 0;
+         t.batch_team_n <= (1 << 24) && t.batch_team_blocks >= 2 && t.batch_team_blocks <= 16 &&
+         t.warp_resolve_row >= 0 && t.warp_resolve_row <= (1 << 24);
 }
 
 Tuning device_tuning(const cc_tuning& t) {
-  return Tuning{t.walk_batches, t.prefetch_ahead, t.inline_heavy, t.inline_decide, t.inline_rebuild, t.heavy_shift};
+  return Tuning{t.walk_batches, t.prefetch_ahead, t.inline_heavy, t.inline_decide, t.inline_rebuild, t.heavy_shift,
+                t.warp_resolve_row};
 }
 
 std::mutex g_tune_mu;
@@ -757,6 +759,7 @@ int cc_graph_get_tuning(const cc_graph* g, cc_tuning* out) {
   out->inline_decide = g->tune.inline_decide;
   out->inline_rebuild = g->tune.inline_rebuild;
   out->heavy_shift = g->tune.heavy_shift;
+  out->warp_resolve_row = g->tune.warp_resolve_row;
   return CC_OK;
 }
 

@@ -41,6 +41,11 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
 __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 __device__ __forceinline__ int ld_volatile_int(const int* p) {
   return *reinterpret_cast<const volatile int*>(p);
 }
@@ -72,6 +77,15 @@ template <class T>
 __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(FULL, x, o);
+  return x;
+}
+
+__device__ __forceinline__ int32_t warp_min_i32(int32_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int32_t y = __shfl_xor_sync(FULL, x, o);
+    x = y < x ? y : x;
+  }
   return x;
 }
 

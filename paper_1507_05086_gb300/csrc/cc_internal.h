@@ -61,6 +61,7 @@ struct Ctl {
   long long r_centers, r_attached, r_noncenter, r_blocked;
   long long undecided;
   unsigned long long h_pack;      // heavy-list appends
+  unsigned long long blk_maxlen;  // C4: longest row of a blocked active this round
   int32_t r0;
   int64_t cursor_next;
   // objective tallies: member-center edges, member-member edges (counted from
@@ -84,6 +85,7 @@ struct Tuning {
   int32_t inline_decide;     // C4 blocked lists up to this long are decided inside the barrier
   int32_t inline_rebuild;    // degree-order segments up to this long are read by the coordinator
   int32_t heavy_shift;       // heavy-list threshold tau = max(1, D >> heavy_shift)
+  int32_t warp_resolve_row;  // C4: blocked sets with rows up to this long resolved one warp per vertex
 };
 Tuning default_tuning();
 // Process-wide settings of batched jobs (cc_set_batch_tuning): the size

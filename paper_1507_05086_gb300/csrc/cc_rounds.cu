@@ -63,6 +63,9 @@ constexpr int32_t kInlineH = 8192;           // heavy lists up to this size are 
 constexpr int32_t kInlineDecide = 4096;      // C4 blocked lists up to this size are decided by the coordinator
 constexpr int32_t kInlineRebuild = 8192;     // heavy-list rebuilds over prefixes up to this size run in the coordinator
 constexpr int32_t kHeavyShift = 1;           // heavy-list threshold tau = max(1, D >> kHeavyShift)
+// C4 blocked actives are resolved one warp each (one grid phase) when every
+// one of them has a warp and no blocked row is longer than this
+constexpr int32_t kWarpResolveRow = 1024;
 
 // State word of a vertex (uint32):
 //   alive ........... kAlive | residual degree
@@ -421,7 +424,7 @@ struct K {
         c.win_len = c.batch_end - c.cursor;
       }
       c.r_edges = 0;
-      C->act_pack = 0; C->new_pack = 0; C->blk_pack = 0;
+      C->act_pack = 0; C->new_pack = 0; C->blk_pack = 0; C->blk_maxlen = 0;
       C->r_centers = 0; C->r_attached = 0; C->r_noncenter = 0; C->r_blocked = 0;
       C->r0 = -1;
       p.state = kRun;
@@ -1247,7 +1250,85 @@ struct K {
         }
       }
       warp_append_rows(blocked, (int32_t)j, row, len, 0x7FFFFFFF, blk_list());
+      const int64_t ml = warp_max<int64_t>(len);
+      if (lane == 0 && ml > 0) atomicMax(&C->blk_maxlen, (unsigned long long)ml);
     }
+  }
+
+  // C4, a round's blocked actives one warp each (every one has a warp of its
+  // own and no row is longer than warp_resolve_row): the warp waits until each
+  // earlier-ranked active neighbour of its vertex is decided; the vertex is a
+  // center iff none of them is a center (isCenter), otherwise it joins the
+  // lowest-ranked one (every earlier center is known by then, so the label is
+  // final at once).  A center then pushes its rank to its alive neighbours
+  // (createCluster).  Waits go only to strictly earlier ranks and every vertex
+  // has a resident warp, so the earliest undecided vertex always progresses:
+  // the same decisions as the fixpoint, in one grid phase.  Every wait is
+  // bounded.
+  __device__ void c4_resolve_by_warp() {
+    const int64_t bn = P().b_n;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)(threadIdx.x >> 5) * G + bid;     // warps numbered across the blocks first
+    const uint32_t tag = (uint32_t)P().tag;
+    const int32_t r0 = P().r0;
+    int32_t v = 0, rv = 0;
+    int64_t row = 0, len = 0;
+    if (gw < bn) {                                                 // warp-uniform
+      const int32_t j = ldcg(B.b_j + gw);
+      v = ldcg(B.act_v + j);
+      rv = ldcg(B.act_r + j);
+      row = ldcg(B.b_e + gw) + ldcg(B.b_d + gw);
+      len = __ldg(B.off + v + 1) - __ldg(B.off + v);
+    }
+    int32_t minc = 0x7FFFFFFF;
+    bool late = false;
+    const uint64_t t0 = globaltimer_ns();
+    for (int64_t base = 0; base < len; base += 32) {
+      const int64_t e = base + lane;
+      if (e >= len || late) continue;
+      const int32_t u = __ldg(B.col + row + e);
+      if (rtag_of(B.rtag, u) != tag) continue;                     // not an active of this round
+      uint32_t x = ldcg(B.st + u);
+      if (!is_active(x)) continue;                                 // a decided non-center, or attached
+      const int32_t ru = ldcg(B.arank + u);
+      if (ru < r0 || ru >= rv) continue;                           // not earlier in this round
+      unsigned spins = 0;
+      while (x == kActive) {
+        if ((++spins & 63) == 0 && (globaltimer_ns() - t0 > kBarrierLimitNs || ld_volatile_int(&C->err) != kOk)) {
+          late = true;
+          break;
+        }
+        x = ld_relaxed_u32(B.st + u);
+      }
+      if (x == kActCenter) minc = ru < minc ? ru : minc;
+    }
+    if (__any_sync(FULL, late)) {
+      if (lane == 0) fail(kErrTimeout);
+      return;
+    }
+    minc = warp_min_i32(minc);
+    const bool center = gw < bn && minc == 0x7FFFFFFF;
+    if (gw < bn && lane == 0) {
+      if (center) {
+        atomicExch(B.st + v, kActCenter);
+        t.centers += 1;
+      } else {
+        atomicExch(B.st + v, kLab + (uint32_t)minc);
+        t.noncenter += 1;
+      }
+    }
+    // a non-center leaves with its row (the removal phase walks it)
+    warp_append_rows(gw < bn && !center && lane == 0, v, row, len, 0, new_list());
+    if (!center) return;
+    for (int64_t base = 0; base < len; base += 32) {
+      const int64_t e = base + lane;
+      const bool in = e < len;
+      const int32_t u = in ? __ldg(B.col + row + e) : 0;
+      const uint32_t tg = in ? rtag_of(B.rtag, u) : 16u;
+      const uint32_t x = tg == 0 ? 0xFFFFFFFFu : (tg == tag ? ldcg(B.st + u) : 0u);
+      attach_one(in, u, rv, x);
+    }
+    append_flush(app_buf(), new_list());
   }
 
   // C4 fixpoint, step 1: look at the earlier active neighbours of every
@@ -1463,11 +1544,17 @@ __device__ void run_job(K& k, int algo) {
                 S.plan.undecided = S.plan.b_n;
                 S.co.fix_iter = 0;
                 S.co.r_edges += 2 * S.plan.b_E;       // first fixpoint scan, blocked attach / pull
+                const int64_t warps = (int64_t)k.G * (blockDim.x >> 5);
+                S.plan.pad4 = (S.plan.b_n > 0 && S.plan.b_n <= warps &&
+                               (int64_t)vload(&C->blk_maxlen) <= (int64_t)k.B.tune.warp_resolve_row) ? 1 : 0;
               }
               k.co_lists_ready();
             }))
           goto out;
-        if (S.plan.b_n > 0) {
+        if (S.plan.b_n > 0 && S.plan.pad4 == 1) {
+          k.c4_resolve_by_warp();
+          if (!k.sync(5, [&] { k.co_lists_ready(); })) goto out;
+        } else if (S.plan.b_n > 0) {
           // the pull slots were set when the list was built; the hit flags are zero
           auto after_decide = [&](long long left) {
             if (threadIdx.x == 0) {
@@ -1809,7 +1896,7 @@ __global__ void k_finalize_labels(RoundBuffers B, int32_t* __restrict__ labels) 
 }  // namespace
 
 Tuning default_tuning() {
-  return Tuning{kLbsBatches, kLbsPfAhead, kInlineH, kInlineDecide, kInlineRebuild, kHeavyShift};
+  return Tuning{kLbsBatches, kLbsPfAhead, kInlineH, kInlineDecide, kInlineRebuild, kHeavyShift, kWarpResolveRow};
 }
 
 size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {

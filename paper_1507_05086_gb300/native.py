@@ -45,7 +45,7 @@ TUNING_FIELDS = (("walk_batches", ctypes.c_int32), ("prefetch_ahead", ctypes.c_i
                  ("inline_heavy", ctypes.c_int32), ("inline_decide", ctypes.c_int32),
                  ("inline_rebuild", ctypes.c_int32), ("heavy_shift", ctypes.c_int32),
                  ("batch_small_n", ctypes.c_int64), ("batch_team_n", ctypes.c_int64),
-                 ("batch_team_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32))
+                 ("batch_team_blocks", ctypes.c_int32), ("warp_resolve_row", ctypes.c_int32))
 
 
 class Tuning(ctypes.Structure):
@@ -53,7 +53,7 @@ class Tuning(ctypes.Structure):
     _fields_ = list(TUNING_FIELDS)
 
     def to_dict(self):
-        return {f: int(getattr(self, f)) for f, _ in TUNING_FIELDS if f != "reserved"}
+        return {f: int(getattr(self, f)) for f, _ in TUNING_FIELDS}
 
     @classmethod
     def from_dict(cls, d):

@@ -76,7 +76,7 @@ def test_tuning_validation_without_gpu():
     assert t["walk_batches"] == 4 and t["heavy_shift"] == 1 and t["batch_team_blocks"] == 8
     for k, bad in (("walk_batches", 0), ("walk_batches", 9), ("prefetch_ahead", -1), ("heavy_shift", 0),
                    ("heavy_shift", 5), ("inline_heavy", 70000), ("batch_team_blocks", 1),
-                   ("batch_team_blocks", 17), ("batch_small_n", 0)):
+                   ("batch_team_blocks", 17), ("batch_small_n", 0), ("warp_resolve_row", -1)):
         with pytest.raises(cc.CCError) as ei:
             cc.set_batch_tuning(dict(t, **{k: bad}))
         assert ei.value.status == -1

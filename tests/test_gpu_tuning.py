@@ -10,9 +10,9 @@ STAT_FIELDS = ("n_alive", "delta", "k", "centers", "removed", "blocked")
 EXTREMES = [
     {},
     {"walk_batches": 1, "prefetch_ahead": 0, "inline_heavy": 0, "inline_rebuild": 0, "inline_decide": 0,
-     "heavy_shift": 4},
+     "heavy_shift": 4, "warp_resolve_row": 0},
     {"walk_batches": 8, "prefetch_ahead": 8, "inline_heavy": 65536, "inline_rebuild": 65536,
-     "inline_decide": 65536, "heavy_shift": 2},
+     "inline_decide": 65536, "heavy_shift": 2, "warp_resolve_row": 1 << 24},
     {"walk_batches": 2, "prefetch_ahead": 1, "inline_heavy": 16, "inline_rebuild": 16, "inline_decide": 1,
      "heavy_shift": 3},
 ]
