@@ -1101,20 +1101,28 @@ struct K {
         }
       }
       if (!sync(3, [&] {
+            // the four words this decision reads, loaded side by side
+            if (threadIdx.x < 4) {
+              const int i = threadIdx.x;
+              S->bcast[i] = i == 0 ? (int64_t)(ldcg(B.desc + G) & kDescVal)
+                                   : i == 1 ? (int64_t)vload(&C->r0)
+                                   : i == 2 ? vload(&C->cursor_next) : (int64_t)vload(&C->act_pack);
+            }
+            __syncthreads();
             if (threadIdx.x == 0) {
               Coord& c = co();
               Plan& p = S->plan;
               // the last block's inclusive prefix: the window's alive count
-              const int64_t total = (int64_t)(ldcg(B.desc + G) & kDescVal);
+              const int64_t total = S->bcast[0];
               p.take = total < c.need ? total : c.need;
               if (c.est) { c.k = total; p.k = total; }   // Sec. 5: all of the window
-              if (p.r0 < 0) p.r0 = vload(&C->r0);
+              if (p.r0 < 0) p.r0 = (int32_t)S->bcast[1];
               const int64_t left = c.est ? 0 : c.need - p.take;
               c.need = left;
               p.need = left;
               if (left == 0) {
-                c.cursor = c.est ? c.batch_end : vload(&C->cursor_next);
-                const unsigned long long pk = vload(&C->act_pack);
+                c.cursor = c.est ? c.batch_end : S->bcast[2];
+                const unsigned long long pk = (unsigned long long)S->bcast[3];
                 p.act_n = (int64_t)(pk >> kPackShift);
                 p.act_E = (int64_t)(pk & kPackEdgeMask);
                 // adjacency passes over the active rows: attach (and C4 detection)
@@ -1537,8 +1545,10 @@ __device__ void run_job(K& k, int algo) {
         k.c4_classify();
         k.attach_from_actives(true);
         if (!k.sync(4, [&] {
+              if (threadIdx.x < 2) S.bcast[threadIdx.x] = (int64_t)vload(threadIdx.x == 0 ? &C->blk_pack : &C->blk_maxlen);
+              __syncthreads();
               if (threadIdx.x == 0) {
-                const unsigned long long pk = vload(&C->blk_pack);
+                const unsigned long long pk = (unsigned long long)S.bcast[0];
                 S.plan.b_n = (int64_t)(pk >> kPackShift);
                 S.plan.b_E = (int64_t)(pk & kPackEdgeMask);
                 S.plan.undecided = S.plan.b_n;
@@ -1546,7 +1556,7 @@ __device__ void run_job(K& k, int algo) {
                 S.co.r_edges += 2 * S.plan.b_E;       // first fixpoint scan, blocked attach / pull
                 const int64_t warps = (int64_t)k.G * (blockDim.x >> 5);
                 S.plan.pad4 = (S.plan.b_n > 0 && S.plan.b_n <= warps &&
-                               (int64_t)vload(&C->blk_maxlen) <= (int64_t)k.B.tune.warp_resolve_row) ? 1 : 0;
+                               S.bcast[1] <= (int64_t)k.B.tune.warp_resolve_row) ? 1 : 0;
               }
               k.co_lists_ready();
             }))
