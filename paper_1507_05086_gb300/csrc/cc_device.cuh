@@ -55,6 +55,23 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
   return t;
 }
 
+// Bounds checks of the debug build (nvcc -DCC_DEBUG; build(debug=True)): an
+// index outside [0, cap) records CC_ERR_INTERNAL in the kernel's error word
+// and the access is skipped, so a bookkeeping mistake reports an error
+// instead of touching memory out of range.  Release builds compile the
+// checks away.
+#ifdef CC_DEBUG
+constexpr bool kDebugChecks = true;
+#else
+constexpr bool kDebugChecks = false;
+#endif
+__device__ __forceinline__ bool in_bounds(int64_t i, int64_t cap, int* err) {
+  if (!kDebugChecks) return true;
+  if (i >= 0 && i < cap) return true;
+  if (err) atomicCAS(err, kOk, kErrInternal);
+  return false;
+}
+
 // Every spin-wait of the kernels is bounded: after kBarrierLimitNs the waiter
 // records kErrTimeout in the error word and the kernel unwinds.
 constexpr uint64_t kBarrierLimitNs = 4000000000ull;   // 4 s
@@ -431,6 +448,8 @@ struct RowList {
   int64_t* delta;
   int32_t* aux;                 // optional per-item payload (may be null)
   unsigned long long* counter;  // packed (items << 33 | edges)
+  int64_t cap;                  // items the arrays hold (checked in debug builds)
+  int* err;                     // error word for a failed check (debug builds)
 };
 
 // Warp-aggregated append of one item per lane with want == true.  All 32
@@ -451,6 +470,7 @@ __device__ __forceinline__ void warp_append_rows(bool want, int32_t v, int64_t r
   if (want) {
     const int64_t j = (int64_t)(old >> kPackShift) + __popc(mask & ((1u << lane) - 1u));
     const int64_t ep = (int64_t)(old & kPackEdgeMask) + ex;
+    if (!in_bounds(j, L.cap, L.err)) return;
     L.v[j] = v;
     L.epos[j] = ep;
     L.delta[j] = row - ep;
@@ -491,7 +511,7 @@ __device__ __forceinline__ void append_flush(AppendBuf* b, const RowList& L) {
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const int i = lane * kPer + q;
-    if (i < n) {
+    if (i < n && in_bounds(j0 + i, L.cap, L.err)) {
       L.v[j0 + i] = b->v[i];
       L.epos[j0 + i] = ep;
       L.delta[j0 + i] = b->row[i] - ep;

@@ -73,21 +73,29 @@ _lock = threading.Lock()
 _lib = None
 
 
+def debug_build_requested() -> bool:
+    """CC_DEBUG_BUILD=1 in the environment selects the bounds-checked library."""
+    return os.environ.get("CC_DEBUG_BUILD", "") not in ("", "0")
+
+
 def lib_path() -> str:
-    return _build.LIB
+    return _build.LIB_DEBUG if debug_build_requested() else _build.LIB
 
 
 def load(build_if_missing: bool = True):
-    """Load libcc.so (building it first if it is missing or stale)."""
+    """Load libcc.so (building it first if it is missing or stale); the
+    bounds-checked variant when CC_DEBUG_BUILD=1."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        if build_if_missing and not _build.up_to_date():
-            _build.build()
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"CUDA library not built: {_build.LIB} (run paper_1507_05086_gb300.build)")
-        lib = ctypes.CDLL(_build.LIB)
+        debug = debug_build_requested()
+        path = _build.LIB_DEBUG if debug else _build.LIB
+        if build_if_missing and not _build.up_to_date(debug):
+            _build.build(debug=debug)
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} (run paper_1507_05086_gb300.build)")
+        lib = ctypes.CDLL(path)
         vp, i64, i32, u32, u64, ci = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32,
                                        ctypes.c_uint64, ctypes.c_int)
         lib.cc_status_string.restype = ctypes.c_char_p
