@@ -55,6 +55,7 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanU = 4;                    // list entries per thread per scan step
+constexpr int64_t kDescStride = 16;          // look-back descriptors: one per 128-byte line
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
 constexpr int kRun = 0, kDone = 1, kAbort = 3, kRebuildDelta = 4, kScanH = 5, kDrawBatch = 6;
 constexpr int kRebuildDeg = 7, kRebuildHeavy = 8;   // Delta search over the degree order, heavy refill
@@ -986,11 +987,13 @@ struct K {
   }
 
   // Look-back over the team (one pass instead of count, barrier, emit):
-  // block bid publishes its alive count in desc[bid], tagged with the barrier
+  // block bid publishes its alive count in desc[bid * kDescStride] (one
+  // 128-byte line per block, so that the pollers of different blocks'
+  // counts meet in different L2 slices), tagged with the barrier
   // epoch; thread q of the block waits for the counts of predecessors q,
   // q + blockDim.x, ... and the block sums them (a single round of loads
   // while the team has at most blockDim.x blocks).  The last block also
-  // stores the window's total in desc[G] for the coordinator.  A cleared
+  // stores the window's total in desc[G * kDescStride] for the coordinator.  A cleared
   // descriptor (flag 0) is never taken for a count, whatever the epoch.
   // Returns this block's exclusive prefix to every thread; every wait is
   // bounded.
@@ -1001,12 +1004,12 @@ struct K {
   }
   __device__ long long lookback(long long mine) {
     volatile unsigned long long* d = B.desc;
-    if (threadIdx.x == 0) d[bid] = pack_desc(1, mine);
+    if (threadIdx.x == 0) d[(int64_t)bid * kDescStride] = pack_desc(1, mine);
     const unsigned tag = epoch & 0xFFFFFFu;
     long long v = 0;
     const uint64_t t0 = globaltimer_ns();
     for (int64_t q = threadIdx.x; q < (int64_t)bid; q += blockDim.x) {
-      unsigned long long x = d[q];
+      unsigned long long x = d[q * kDescStride];
       unsigned spins = 0;
       while ((unsigned)(x >> 40) != tag || ((x >> 38) & 3u) == 0) {
         if ((++spins & 63) == 0 && (ld_volatile_int(&C->err) != kOk || globaltimer_ns() - t0 > kBarrierLimitNs)) {
@@ -1014,12 +1017,12 @@ struct K {
           x = 0;
           break;
         }
-        x = d[q];
+        x = d[q * kDescStride];
       }
       v += (long long)(x & kDescVal);
     }
     const long long excl = block_sum<int64_t>(v, S->scr);
-    if (threadIdx.x == 0 && bid == G - 1) d[G] = pack_desc(2, excl + mine);
+    if (threadIdx.x == 0 && bid == G - 1) d[(int64_t)G * kDescStride] = pack_desc(2, excl + mine);
     return excl;
   }
 
@@ -1107,7 +1110,7 @@ struct K {
             // the four words this decision reads, loaded side by side
             if (threadIdx.x < 4) {
               const int i = threadIdx.x;
-              S->bcast[i] = i == 0 ? (int64_t)(ldcg(B.desc + G) & kDescVal)
+              S->bcast[i] = i == 0 ? (int64_t)(ldcg(B.desc + (int64_t)G * kDescStride) & kDescVal)
                                    : i == 1 ? (int64_t)vload(&C->r0)
                                    : i == 2 ? vload(&C->cursor_next) : (int64_t)vload(&C->act_pack);
             }
@@ -1628,7 +1631,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_rounds(const __grid_constant__ 
   if (threadIdx.x < 5) S.tal[threadIdx.x] = 0;
   // look-back descriptors of an earlier launch could carry the same epochs:
   // clear this block's before the first barrier
-  if (threadIdx.x == 0) B.desc[blockIdx.x] = 0;
+  if (threadIdx.x == 0) B.desc[(int64_t)blockIdx.x * kDescStride] = 0;
   __syncthreads();
   run_job(k, vload(&B.ctl->algo));
 }
@@ -1800,7 +1803,7 @@ k_batch(BatchJob* __restrict__ jobs, int njobs, const RoundBuffers* __restrict__
     // zero the permutation counters, reset the control block (not the barrier counters)
     const int64_t zn = 2 * (int64_t)kPermMaxBuckets + 2;
     for (int64_t i = (int64_t)k.bid * blockDim.x + threadIdx.x; i < zn; i += (int64_t)G * blockDim.x) rb.pcnt[i] = 0;
-    if (threadIdx.x == 0) rb.desc[k.bid] = 0;   // look-back descriptors of an earlier launch
+    if (threadIdx.x == 0) rb.desc[(int64_t)k.bid * kDescStride] = 0;   // look-back descriptors of an earlier launch
     if (!k.sync(7, [&] {
           if (threadIdx.x == 0) {
             C->err = 0;
@@ -1929,7 +1932,8 @@ size_t rounds_workspace_bytes(int64_t n, int32_t max_deg, int grid) {
   b += 3 * align_up(nn);                 // blk_flag, hit_c, hit_p
   b += align_up(4 * nn);                 // pull
   b += align_up(4 * nn) + 2 * align_up(8 * nn);       // b_j, b_e, b_d
-  b += 3 * align_up(8 * ((size_t)grid + 1));          // blk_a, blk_b, desc
+  b += 2 * align_up(8 * ((size_t)grid + 1));          // blk_a, blk_b
+  b += align_up(8 * kDescStride * ((size_t)grid + 1)); // desc
   return b;
 }
 
@@ -1962,7 +1966,7 @@ void rounds_carve(void* ws, int64_t n, int32_t max_deg, int grid, RoundBuffers* 
   B->b_d = reinterpret_cast<int64_t*>(take(8 * nn));
   B->blk_a = reinterpret_cast<int64_t*>(take(8 * ((size_t)grid + 1)));
   B->blk_b = reinterpret_cast<int64_t*>(take(8 * ((size_t)grid + 1)));
-  B->desc = reinterpret_cast<unsigned long long*>(take(8 * ((size_t)grid + 1)));
+  B->desc = reinterpret_cast<unsigned long long*>(take(8 * kDescStride * ((size_t)grid + 1)));
 }
 
 int rounds_grid_size(int device) {
