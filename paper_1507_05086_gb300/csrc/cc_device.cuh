@@ -71,6 +71,16 @@ __device__ __forceinline__ bool in_bounds(int64_t i, int64_t cap, int* err) {
   if (err) atomicCAS(err, kOk, kErrInternal);
   return false;
 }
+// The checks as written at the access sites: in release builds the macro is
+// the constant true and its arguments are not compiled at all, so the kernels
+// are the same code as without the checks (register allocation included).
+#ifdef CC_DEBUG
+#define CC_IN_BOUNDS(i, cap, err) in_bounds((i), (cap), (err))
+#define CC_ROWLIST_CHECK(cap, err) , (cap), (err)
+#else
+#define CC_IN_BOUNDS(i, cap, err) true
+#define CC_ROWLIST_CHECK(cap, err)
+#endif
 
 // Every spin-wait of the kernels is bounded: after kBarrierLimitNs the waiter
 // records kErrTimeout in the error word and the kernel unwinds.
@@ -448,8 +458,10 @@ struct RowList {
   int64_t* delta;
   int32_t* aux;                 // optional per-item payload (may be null)
   unsigned long long* counter;  // packed (items << 33 | edges)
-  int64_t cap;                  // items the arrays hold (checked in debug builds)
-  int* err;                     // error word for a failed check (debug builds)
+#ifdef CC_DEBUG
+  int64_t cap;                  // items the arrays hold
+  int* err;                     // error word for a failed check
+#endif
 };
 
 // Warp-aggregated append of one item per lane with want == true.  All 32
@@ -470,7 +482,7 @@ __device__ __forceinline__ void warp_append_rows(bool want, int32_t v, int64_t r
   if (want) {
     const int64_t j = (int64_t)(old >> kPackShift) + __popc(mask & ((1u << lane) - 1u));
     const int64_t ep = (int64_t)(old & kPackEdgeMask) + ex;
-    if (!in_bounds(j, L.cap, L.err)) return;
+    if (!CC_IN_BOUNDS(j, L.cap, L.err)) return;
     L.v[j] = v;
     L.epos[j] = ep;
     L.delta[j] = row - ep;
@@ -511,7 +523,7 @@ __device__ __forceinline__ void append_flush(AppendBuf* b, const RowList& L) {
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
     const int i = lane * kPer + q;
-    if (i < n && in_bounds(j0 + i, L.cap, L.err)) {
+    if (i < n && CC_IN_BOUNDS(j0 + i, L.cap, L.err)) {
       L.v[j0 + i] = b->v[i];
       L.epos[j0 + i] = ep;
       L.delta[j0 + i] = b->row[i] - ep;

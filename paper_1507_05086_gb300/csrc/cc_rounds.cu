@@ -328,9 +328,9 @@ struct K {
     return sync(cat, [] {});
   }
 
-  __device__ RowList new_list() const { return RowList{B.new_v, B.new_e, B.new_d, nullptr, &C->new_pack, B.n, &C->err}; }
+  __device__ RowList new_list() const { return RowList{B.new_v, B.new_e, B.new_d, nullptr, &C->new_pack CC_ROWLIST_CHECK(B.n, &C->err)}; }
   // blocked actives; the payload initialises each one's pull slot (no center yet)
-  __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, B.pull, &C->blk_pack, B.n, &C->err}; }
+  __device__ RowList blk_list() const { return RowList{B.b_j, B.b_e, B.b_d, B.pull, &C->blk_pack CC_ROWLIST_CHECK(B.n, &C->err)}; }
   __device__ LbsWarp* lbs_ws() const { return &S->u.w.lbs[threadIdx.x >> 5]; }
   __device__ AppendBuf* app_buf() const { return &S->u.w.app[threadIdx.x >> 5]; }
 
@@ -604,7 +604,7 @@ struct K {
             if (is_alive(x[q]) && deg_of(x[q]) > 0 && (int64_t)deg_of(x[q]) >= tau)
             {
               const int64_t h = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(&S->bcast[0]), 1ull);
-              if (in_bounds(h, B.n, &C->err)) B.hv[h] = v[q];
+              if (CC_IN_BOUNDS(h, B.n, &C->err)) B.hv[h] = v[q];
             }
         }
         __syncthreads();
@@ -832,8 +832,8 @@ struct K {
 #pragma unroll
       for (int q = 0; q < kScanU; ++q) {
         if (d[q] == 0) continue;
-        if (in_bounds(o, B.n, &C->err)) dst[o++] = v[q];
-        if ((int64_t)d[q] >= tau && in_bounds(ho, B.n, &C->err)) B.hv[ho++] = v[q];
+        if (CC_IN_BOUNDS(o, B.n, &C->err)) dst[o++] = v[q];
+        if ((int64_t)d[q] >= tau && CC_IN_BOUNDS(ho, B.n, &C->err)) B.hv[ho++] = v[q];
       }
       run += tot;
     }
@@ -911,7 +911,7 @@ struct K {
       }
 #pragma unroll
       for (int q = 0; q < kScanU; ++q)
-        if (v[q] >= 0 && in_bounds(ho, B.n, &C->err)) B.hv[ho++] = v[q];
+        if (v[q] >= 0 && CC_IN_BOUNDS(ho, B.n, &C->err)) B.hv[ho++] = v[q];
     }
     return sync(1, [&] { finish_rebuild(co().rb_D, (int64_t)vload(&C->h_pack)); });
   }
@@ -975,7 +975,7 @@ struct K {
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < kScanU; ++q) {
-      if (!listed[q] || !in_bounds(j, B.n, &C->err)) continue;
+      if (!listed[q] || !CC_IN_BOUNDS(j, B.n, &C->err)) continue;
       B.act_v[j] = a[q].y;
       B.act_r[j] = a[q].x;
       B.act_e[j] = ep;
@@ -1183,7 +1183,7 @@ struct K {
     // degree 1: nothing to decrement, and no other center can reach it, so
     // its label is already final.
     const bool single = fresh && d_old == 1;
-    if (single && in_bounds(r, B.n, &C->err)) atomicAdd(B.size + r, 1);   // one more member (result unused)
+    if (single && CC_IN_BOUNDS(r, B.n, &C->err)) atomicAdd(B.size + r, 1);   // one more member (result unused)
     const bool want = fresh && d_old != 1;
     int64_t row = 0;
     int32_t len = 0;
@@ -1204,7 +1204,7 @@ struct K {
       for (int q = 0; q < kLbsK; ++q) {
         push[q] = L.ok(q) && (!skip_blocked || ldcg(B.blk_flag + L.item(q)) == 0);
         u[q] = push[q] ? __ldg(B.col + L.csr(q)) : 0;
-        if (push[q] && !in_bounds(u[q], B.n, &C->err)) push[q] = false;
+        if (push[q] && !CC_IN_BOUNDS(u[q], B.n, &C->err)) push[q] = false;
       }
       // alive (tag 0): try the atomicMin directly; tagged this round (or 15k
       // rounds ago): the state word decides; removed earlier: nothing to do
@@ -1453,16 +1453,14 @@ struct K {
     lbs(B.new_e, nn, nE, [&](const Lbs& L) {
       int32_t w[kLbsK];
       uint32_t lu[kLbsK], x[kLbsK];
-      bool ok[kLbsK];
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
         w[q] = L.ok(q) ? __ldg(B.col + L.csr(q)) : 0;
-        ok[q] = L.ok(q) && in_bounds(w[q], B.n, &C->err);
         lu[q] = (uint32_t)L.vtx(q);                             // the member's (final) label
       }
       uint32_t tg[kLbsK];
 #pragma unroll
-      for (int q = 0; q < kLbsK; ++q) tg[q] = ok[q] ? rtag_of(B.rtag, w[q]) : 16u;
+      for (int q = 0; q < kLbsK; ++q) tg[q] = L.ok(q) && CC_IN_BOUNDS(w[q], B.n, &C->err) ? rtag_of(B.rtag, w[q]) : 16u;
       // alive: decrement; maybe removed this round: the state word decides
       // whether w shares the member's cluster; removed earlier: nothing
       const uint32_t tag = (uint32_t)P().tag;
@@ -1470,8 +1468,8 @@ struct K {
       for (int q = 0; q < kLbsK; ++q) x[q] = tg[q] == tag ? ldcg(B.st + w[q]) : 0;
 #pragma unroll
       for (int q = 0; q < kLbsK; ++q) {
-        if (!ok[q]) continue;
-        if (L.in_row(q) == 0 && in_bounds(lu[q], B.n, &C->err)) atomicAdd(B.size + lu[q], 1);   // once per removed member
+        if (!L.ok(q) || !CC_IN_BOUNDS(w[q], B.n, &C->err)) continue;
+        if (L.in_row(q) == 0 && CC_IN_BOUNDS(lu[q], B.n, &C->err)) atomicAdd(B.size + lu[q], 1);   // once per removed member
         if (tg[q] == 0) {
           atomicSub(B.st + w[q], 1u);                          // result unused
         } else if (tg[q] != tag) {
