@@ -44,8 +44,11 @@ BATCH_KNOBS = {
 
 
 def default_cache_path() -> str:
-    return os.environ.get("CC_TUNING_CACHE",
-                          os.path.join(os.path.expanduser("~"), ".cache", "paper_1507_05086_gb300", "tuning.json"))
+    """$CC_TUNE_CACHE (or $CC_TUNING_CACHE), else a file under ~/.cache."""
+    for var in ("CC_TUNE_CACHE", "CC_TUNING_CACHE"):
+        if os.environ.get(var):
+            return os.environ[var]
+    return os.path.join(os.path.expanduser("~"), ".cache", "paper_1507_05086_gb300", "tuning.json")
 
 
 def device_key() -> str:

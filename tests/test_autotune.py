@@ -83,3 +83,13 @@ def test_tuning_validation_without_gpu():
     with pytest.raises(cc.CCError):
         cc.set_batch_tuning(dict(t, batch_team_n=t["batch_small_n"] - 1))
     assert cc.get_batch_tuning() == t
+
+
+def test_cache_path_from_environment(tmp_path, monkeypatch):
+    monkeypatch.delenv("CC_TUNE_CACHE", raising=False)
+    monkeypatch.delenv("CC_TUNING_CACHE", raising=False)
+    assert autotune.default_cache_path().endswith("tuning.json")
+    monkeypatch.setenv("CC_TUNING_CACHE", str(tmp_path / "b.json"))
+    assert autotune.default_cache_path() == str(tmp_path / "b.json")
+    monkeypatch.setenv("CC_TUNE_CACHE", str(tmp_path / "a.json"))
+    assert autotune.default_cache_path() == str(tmp_path / "a.json")
