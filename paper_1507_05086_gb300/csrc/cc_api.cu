@@ -13,6 +13,7 @@
 #include "cc_async.h"
 #include "cc_graph_impl.h"
 #include "cc_internal.h"
+#include "cc_nvtx.h"
 
 using namespace ccg;
 
@@ -245,6 +246,7 @@ int cc_graph_destroy(cc_graph* g) {
 
 int cc_graph_create(int64_t n, const void* row_offsets, const int32_t* col_idx, uint32_t flags,
                     void* cuda_stream, cc_graph** out) {
+  NvtxRange range("cc_graph_create");
   if (!out) return CC_ERR_INVALID_ARG;
   *out = nullptr;
   if (n < 0 || n > 2147483616LL || !row_offsets) return CC_ERR_INVALID_ARG;
@@ -479,6 +481,7 @@ static int cluster_async(cc_graph* g, uint64_t seed, int32_t* labels_out, int32_
 
 int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels_out, int32_t* rounds_out,
                   int64_t* disagreements_out, cc_round_stats* stats, int32_t stats_cap, int32_t* stats_len) {
+  NvtxRange range("cc_cluster");
   if (!g) return CC_ERR_INVALID_ARG;
   // the test hook belongs to this call whatever its outcome (a bad argument,
   // an empty graph, a failed allocation, the asynchronous algorithm)
@@ -522,10 +525,17 @@ int cc_cluster_ex(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* lab
   b.stats_cap = stats_cap;
   CC_TRY(cudaMemsetAsync(g->perm_err, 0, sizeof(int), s));
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[0], s));
-  CC_TRY(launch_permutation(g->n, seed, g->order, g->perm_ws, g->num_sms, g->perm_err, s));
+  {
+    NvtxRange r("permutation");
+    CC_TRY(launch_permutation(g->n, seed, g->order, g->perm_ws, g->num_sms, g->perm_err, s));
+  }
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[1], s));
-  CC_TRY(launch_rounds(b, algo, ppm, seed, g->grid, s, withhold));
+  {
+    NvtxRange r("rounds");
+    CC_TRY(launch_rounds(b, algo, ppm, seed, g->grid, s, withhold));
+  }
   if (g->timing) CC_TRY(cudaEventRecord(g->ev[2], s));
+  NvtxRange labels_range("labels");
   const bool dev = is_device_ptr(labels_out);
   if (labels_out && !dev) {
     if ((rc = ensure_labels_tmp(g)) != CC_OK) return rc;
@@ -599,6 +609,7 @@ int cc_cluster(cc_graph* g, int algo, double eps, uint64_t seed, int32_t* labels
 }
 
 int cc_disagreements(cc_graph* g, const int32_t* labels, int64_t* out) {
+  NvtxRange range("cc_disagreements");
   if (!g || !out || (!labels && g->n > 0)) return CC_ERR_INVALID_ARG;
   if (g->n == 0) { *out = 0; return CC_OK; }
   cudaSetDevice(g->device);
@@ -629,6 +640,7 @@ namespace {
 // and disagreements.
 int run_batch_jobs(cc_graph* const* gs, int32_t count, int algo, double eps, const uint64_t* seeds, int32_t k_perms,
                    std::vector<BatchJob>& jobs) {
+  NvtxRange range("cc_batch_jobs");
   if (count < 0 || k_perms < 1 || (count > 0 && (!gs || !seeds))) return CC_ERR_INVALID_ARG;
   if (algo < CC_ALGO_C4 || algo > CC_ALGO_CLUSTERWILD_EST) return CC_ERR_INVALID_ARG;
   int64_t ppm = 0;

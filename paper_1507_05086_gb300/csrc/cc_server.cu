@@ -40,6 +40,7 @@
 #include "../../include/cc.h"
 #include "cc_graph_impl.h"
 #include "cc_internal.h"
+#include "cc_nvtx.h"
 
 using namespace ccg;
 
@@ -178,6 +179,7 @@ void release_device(Flight& f) {
 // GPU.  Called without the lock held.  On failure everything the call
 // allocated is released and the status returned.
 int start_batch(cc_server* sv, Flight& f, int cls, std::vector<Request>& reqs) {
+  NvtxRange range(cls == kSmall ? "cc_server batch: small" : "cc_server batch: team");
   const int64_t n_max = std::max_element(reqs.begin(), reqs.end(), [](const Request& a, const Request& b) {
                           return a.g->n < b.g->n;
                         })->g->n;
