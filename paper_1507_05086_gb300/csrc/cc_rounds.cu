@@ -55,6 +55,7 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kScanU = 4;                    // list entries per thread per scan step
+constexpr int kSelU = 2;                     // window entries per thread per selection step
 constexpr int64_t kDescStride = 16;          // look-back descriptors: one per 128-byte line
 constexpr int kAlgoC4 = 1, kAlgoCW = 2;
 constexpr int kRun = 0, kDone = 1, kAbort = 3, kRebuildDelta = 4, kScanH = 5, kDrawBatch = 6;
@@ -929,11 +930,11 @@ struct K {
   // Called by every thread of the block for one tile of the window; entry q
   // of a thread is an active vertex (rank a[q].x, vertex a[q].y) when want[q].
   __device__ void emit_actives(const int2* a, const bool* want, int algo) {
-    int64_t deg0[kScanU], row[kScanU];
-    bool listed[kScanU];
+    int64_t deg0[kSelU], row[kSelU];
+    bool listed[kSelU];
     int64_t nl = 0, el = 0;
 #pragma unroll
-    for (int q = 0; q < kScanU; ++q) {
+    for (int q = 0; q < kSelU; ++q) {
       listed[q] = false;
       deg0[q] = 0;
       row[q] = 0;
@@ -974,7 +975,7 @@ struct K {
     int64_t j = S->bcast[0] + jx, ep = S->bcast[1] + ex;
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < kScanU; ++q) {
+    for (int q = 0; q < kSelU; ++q) {
       if (!listed[q] || !CC_IN_BOUNDS(j, B.n, &C->err)) continue;
       B.act_v[j] = a[q].y;
       B.act_r[j] = a[q].x;
@@ -1035,30 +1036,30 @@ struct K {
       // arank): an active of this round is told from an earlier round's
       // center by its rank, which is >= r0, the round's first active rank.
       // count this block's alive entries (the first tile stays in registers)
-      const int64_t tile = (int64_t)blockDim.x * kScanU;
-      int2 a0[kScanU];
-      bool alive0[kScanU];
+      const int64_t tile = (int64_t)blockDim.x * kSelU;
+      int2 a0[kSelU];
+      bool alive0[kSelU];
       int64_t mine0 = 0;
 #pragma unroll
-      for (int q = 0; q < kScanU; ++q) {
-        const int64_t i = s + (int64_t)threadIdx.x * kScanU + q;
+      for (int q = 0; q < kSelU; ++q) {
+        const int64_t i = s + (int64_t)threadIdx.x * kSelU + q;
         a0[q] = i < e ? al_at(i) : make_int2(0, -1);
       }
 #pragma unroll
-      for (int q = 0; q < kScanU; ++q) {
+      for (int q = 0; q < kSelU; ++q) {
         alive0[q] = a0[q].y >= 0 && rtag_of(B.rtag, a0[q].y) == 0;
         mine0 += alive0[q] ? 1 : 0;
       }
       int64_t cnt = mine0;
       for (int64_t base = s + tile; base < e; base += 2 * tile) {
-        int2 a[2 * kScanU];
+        int2 a[2 * kSelU];
 #pragma unroll
-        for (int q = 0; q < 2 * kScanU; ++q) {
+        for (int q = 0; q < 2 * kSelU; ++q) {
           const int64_t i = base + (int64_t)q * blockDim.x + threadIdx.x;
           a[q] = i < e ? al_at(i) : make_int2(0, -1);
         }
 #pragma unroll
-        for (int q = 0; q < 2 * kScanU; ++q)
+        for (int q = 0; q < 2 * kSelU; ++q)
           cnt += (a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0) ? 1 : 0;
       }
       cnt = block_sum<int64_t>(cnt, S->scr);
@@ -1069,36 +1070,36 @@ struct K {
       const bool first_window = P().r0 < 0;
       if (run < need) {
         for (int64_t base = s; base < e; base += tile) {
-          int2 a[kScanU];
-          bool alive[kScanU];
+          int2 a[kSelU];
+          bool alive[kSelU];
           int64_t mine = 0;
           if (base == s) {
 #pragma unroll
-            for (int q = 0; q < kScanU; ++q) {
+            for (int q = 0; q < kSelU; ++q) {
               a[q] = a0[q];
               alive[q] = alive0[q];
             }
             mine = mine0;
           } else {
 #pragma unroll
-            for (int q = 0; q < kScanU; ++q) {
-              const int64_t i = base + (int64_t)threadIdx.x * kScanU + q;
+            for (int q = 0; q < kSelU; ++q) {
+              const int64_t i = base + (int64_t)threadIdx.x * kSelU + q;
               a[q] = i < e ? al_at(i) : make_int2(0, -1);
             }
 #pragma unroll
-            for (int q = 0; q < kScanU; ++q) {
+            for (int q = 0; q < kSelU; ++q) {
               alive[q] = a[q].y >= 0 && rtag_of(B.rtag, a[q].y) == 0;
               mine += alive[q] ? 1 : 0;
             }
           }
           int64_t tot;
           int64_t g = run + block_exclusive_sum<int64_t>(mine, S->scr, &tot);
-          bool want[kScanU];
+          bool want[kSelU];
 #pragma unroll
-          for (int q = 0; q < kScanU; ++q) {
+          for (int q = 0; q < kSelU; ++q) {
             want[q] = alive[q] && g < need;
             if (want[q] && g == 0 && first_window) C->r0 = a[q].x;
-            if (want[q] && g == need - 1) C->cursor_next = base + (int64_t)threadIdx.x * kScanU + q + 1;
+            if (want[q] && g == need - 1) C->cursor_next = base + (int64_t)threadIdx.x * kSelU + q + 1;
             g += alive[q] ? 1 : 0;
           }
           emit_actives(a, want, algo);
